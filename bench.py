@@ -1,0 +1,549 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 VecWXPY library: FP64 w = alpha*x + y.
+
+Timed step: one pass of the size sweep through the C ABI ``wxpy()`` call,
+n = 2^k and 2^k + 3 for k = 10..28 (38 calls), start offsets 0/8/24 bytes by k,
+distinct x, y, w, inputs resident in HBM.  ``value`` is the algorithmic bytes
+(24 per element: read x, read y, write w) of all timed steps over their device
+time, in GB/s.  Each step streams 12.9 GB, far more than the 129 MB L2, so the
+data of one step is gone from L2 when the next step reads it.
+
+Extra measurements in the same JSON line (not in the timed region): GB/s per n
+with the L2 flushed between repetitions and L2-resident; the host-buffer
+end-to-end number (``e2e``); the oracle on the host cores (``cpu_baseline``);
+the clocks sampled during the timed region; and, once built, the batched,
+served and stream-split workloads.
+
+``--impl reference`` times the CPU oracle, as it stands, on a bounded sample of
+the same sweep and prints the same metric with "impl": "reference".
+
+Multi-GPU: one process per GPU (torchrun); each rank runs an independent
+replica of the step on its own GPU (the operation has no exchange step), the
+timing is the max over ranks and ``value`` the sum of all ranks' bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "wxpy achieved HBM GB/s vs peak; batched/served elem/s and p99 vs per-call launch"
+UNIT = "GB/s"
+BYTES_PER_ELEM = 24
+SWEEP_K = range(10, 29)
+OFFSETS = (0, 8, 24)
+DOMINANT_K = 28
+WORKLOAD = ("size sweep of single-call FP64 w = alpha*x + y: n = 2^k and 2^k+3 for "
+            "k = 10..28, start offsets 0/8/24 B by k, distinct x, y, w, 38 calls per step")
+
+
+def sweep_calls():
+    """(n, element offset) of the 38 calls of one step."""
+    calls = []
+    for k in SWEEP_K:
+        for d in (0, 3):
+            calls.append(((1 << k) + d, OFFSETS[k % 3] // 8))
+    return calls
+
+
+# ----------------------------------------------------------------- helpers
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    """Hash of the single-call kernel sources; a profile summary records it, so
+    that a stale ncu traffic figure is never reported against a changed kernel."""
+    h = hashlib.sha256()
+    for name in ("single_kernel.cuh", "kernels_vw4.cu"):
+        with open(os.path.join(ROOT, "paper_1309_1894_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, scaled to n = 2^28 + 3, or None if absent or stale."""
+    path = os.path.join(ROOT, "profiles", "wxpy_single_kernel_traffic.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().split()[0]
+        if fields.get("source_hash") != kernel_source_hash():
+            return None
+        per_elem = float(fields["dram_bytes"]) / float(fields["n"])
+        return per_elem * ((1 << DOMINANT_K) + 3)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+def cpu_oracle_rate(max_k: int, seconds: float, threads: int = 1):
+    """GB/s of the oracle over passes of the sweep restricted to k <= max_k,
+    repeated for about ``seconds``; ``threads`` > 1 splits each call into
+    contiguous chunks run by a thread pool (the oracle function unchanged)."""
+    import numpy as np
+    import oracle
+    from paper_1309_1894_gb300 import synth
+    from concurrent.futures import ThreadPoolExecutor
+
+    nmax = (1 << max_k) + 3
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED, nmax + 3)
+    wh = np.empty_like(xh)
+    calls = [(n, o) for (n, o) in sweep_calls() if n <= nmax]
+    pool = ThreadPoolExecutor(threads) if threads > 1 else None
+
+    def one(n, o):
+        if pool is None:
+            oracle.wxpy_into(alpha, xh[o:o + n], yh[o:o + n], wh[o:o + n])
+            return
+        bounds = [o + (n * t) // threads for t in range(threads + 1)]
+        futs = [pool.submit(oracle.wxpy_into, alpha, xh[a:b], yh[a:b], wh[a:b])
+                for a, b in zip(bounds[:-1], bounds[1:])]
+        for f in futs:
+            f.result()
+
+    for (n, o) in calls:  # warm-up pass
+        one(n, o)
+    passes, byts = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        for (n, o) in calls:
+            one(n, o)
+            byts += BYTES_PER_ELEM * n
+        passes += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    if pool is not None:
+        pool.shutdown()
+    return byts / dt / 1e9, passes, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1309_1894_gb300 import synth
+    max_k = 20  # bounded sample: k = 10..20 per step
+    nmax = (1 << max_k) + 3
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED, nmax + 3)
+    wh = np.empty_like(xh)
+    calls = [(n, o) for (n, o) in sweep_calls() if n <= nmax]
+    step_bytes = sum(BYTES_PER_ELEM * n for n, _ in calls)
+
+    def step():
+        for (n, o) in calls:
+            oracle.wxpy_into(alpha, xh[o:o + n], yh[o:o + n], wh[o:o + n])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = step_bytes * args.steps / dt / 1e9
+    sample = (f"each step: the sweep's calls with k = 10..{max_k} (22 calls, "
+              f"{step_bytes / 1e6:.1f} MB), CPU oracle, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_1309_1894_gb300 as wx
+    from paper_1309_1894_gb300 import synth
+
+    ws, rank, local = dist_env()
+    dist = init_dist(ws)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = wx.lib()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+
+    calls = sweep_calls()
+    nmax = max(n for n, _ in calls)
+    x = torch.empty(nmax + 8, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    w = torch.empty_like(x)
+    seed = synth.BASE_SEED + rank
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    alpha = synth.alpha_scalar(seed)
+    px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
+    cargs = [(n, px + 8 * o, py + 8 * o, pw + 8 * o) for (n, o) in calls]
+    step_bytes = sum(BYTES_PER_ELEM * n for n, _ in calls)
+
+    # launches per call: the variant wxpy() runs, after the stream-split rule
+    launches_per_step = 0
+    variants = {}
+    for (n, o) in calls:
+        v, src = wx.wxpy_lookup(x[o:o + n], y[o:o + n], w[o:o + n])
+        s = v["streams"]
+        while s > 1 and n // s < 65536:
+            s //= 2
+        launches_per_step += s
+        variants[n] = (v, src)
+    dom = [i for i, (n, _) in enumerate(calls) if n >= (1 << DOMINANT_K)]
+
+    def step(ev_pairs=None):
+        for i, (n, a, b, c) in enumerate(cargs):
+            if ev_pairs is not None and i in dom:
+                e0, e1 = ev_pairs.pop()
+                e0.record(stream)
+                rc = lib.wxpy(n, alpha, a, b, c, sh)
+                e1.record(stream)
+            else:
+                rc = lib.wxpy(n, alpha, a, b, c, sh)
+            if rc != 0:
+                wx.check(rc, "wxpy")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(K * len(dom))]
+    used = list(pairs)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start.record(stream)
+        for _ in range(K):
+            step(pairs)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = t_start.elapsed_time(t_end)
+    ms_max = max_over_ranks(dist, ms)
+    total_bytes = sum_over_ranks(dist, step_bytes * K)
+    value = total_bytes / (ms_max / 1e3) / 1e9
+
+    dom_ms = sum(a.elapsed_time(b) for a, b in used)
+    dom_bytes = sum(BYTES_PER_ELEM * calls[i][0] for i in dom) * K
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    peak, peak_src = load_peaks()
+    traffic = profiled_traffic()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step_bytes": step_bytes,
+                   "l2": "inputs larger than L2: each step streams "
+                         f"{step_bytes / 1e9:.1f} GB against a 129 MB L2",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "variant_n_2e28": variants[1 << DOMINANT_K][0],
+                   "variant_source": {0: "default", 1: "tuned", 2: "forced"}[
+                       variants[1 << DOMINANT_K][1]]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "wxpy_single_kernel (n = 2^28 and 2^28+3 launches)",
+                     "peak_source": f"{peak_src} hbm_gbs",
+                     "frac_of_nominal_8TBs": achieved / 8000.0},
+        "gpu_launches": launches_per_step * K,
+    }
+    result["clocks"] = clocks.summary()
+
+    if rank == 0 and not args.no_extras:
+        result["sweep"] = measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak)
+    result["e2e"] = measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist)
+    del x, y, w
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
+        result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
+    if rank == 0:
+        rate1, passes, dt = cpu_oracle_rate(24, args.cpu_seconds, threads=1)
+        cores = host_cores()
+        rate_all, _, _ = cpu_oracle_rate(24, max(2.0, args.cpu_seconds / 3), threads=cores)
+        result["cpu_baseline"] = {
+            "value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{passes} passes over the sweep's calls with k = 10..24 "
+                      f"(30 calls, {dt:.1f} s), single thread",
+            "all_cores": {"value": rate_all, "cores": cores,
+                          "how": "each call split into contiguous chunks, one thread each"}}
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=9):
+    """GB/s per n: median of ``reps`` with the L2 flushed (read of a 512 MB buffer)
+    before each timed call, and L2-resident (back-to-back) for n <= 2^22."""
+    flush = torch.empty(64 << 20, dtype=torch.float64, device=x.device)
+    flush.fill_(1.0)
+    out = []
+    px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
+    for (n, o) in calls:
+        args = (n, alpha, px + 8 * o, py + 8 * o, pw + 8 * o, sh)
+        tf = []
+        for _ in range(reps):
+            flush.sum()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lib.wxpy(*args)
+            e1.record(stream)
+            e1.synchronize()
+            tf.append(e0.elapsed_time(e1))
+        row = {"n": n, "offset_bytes": 8 * o,
+               "gbs_l2_flushed": BYTES_PER_ELEM * n / (statistics.median(tf) / 1e3) / 1e9,
+               "us_l2_flushed": statistics.median(tf) * 1e3}
+        if n <= (1 << 22) + 3:
+            r = 50
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            lib.wxpy(*args)
+            e0.record(stream)
+            for _ in range(r):
+                lib.wxpy(*args)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / r
+            row["gbs_l2_resident"] = BYTES_PER_ELEM * n / (t / 1e3) / 1e9
+        row["frac_of_peak_flushed"] = row["gbs_l2_flushed"] / peak
+        out.append(row)
+    del flush
+    return out
+
+
+def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
+    """The sweep end to end from pinned host memory: per call, copy x and y in,
+    run wxpy, copy w out, all on one stream; bytes counted from the copies."""
+    nmax = max(n for n, _ in calls)
+    steps = max(1, args.e2e_steps)
+    hx = torch.empty(nmax + 8, dtype=torch.float64, pin_memory=True)
+    hy = torch.empty_like(hx, pin_memory=True)
+    hw = torch.empty_like(hx, pin_memory=True)
+    hx.uniform_(-1, 1)
+    hy.uniform_(-1, 1)
+    dx = torch.empty(nmax + 8, dtype=torch.float64, device=dev)
+    dy = torch.empty_like(dx)
+    dw = torch.empty_like(dx)
+    h2d = sum(16 * n for n, _ in calls)
+    d2h = sum(8 * n for n, _ in calls)
+
+    def step():
+        for (n, o) in calls:
+            dx[o:o + n].copy_(hx[o:o + n], non_blocking=True)
+            dy[o:o + n].copy_(hy[o:o + n], non_blocking=True)
+            rc = lib.wxpy(n, alpha, dx.data_ptr() + 8 * o, dy.data_ptr() + 8 * o,
+                          dw.data_ptr() + 8 * o, sh)
+            wx.check(rc, "wxpy")
+            hw[o:o + n].copy_(dw[o:o + n], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    total = sum_over_ranks(dist, sum(BYTES_PER_ELEM * n for n, _ in calls) * steps)
+    del hx, hy, hw, dx, dy, dw
+    return {"value": total / (ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "how": "per call: pinned host x, y -> device, wxpy(), device w -> pinned host, "
+                   "one stream, copies inside the timed region"}
+
+
+def measure_streams(wx, lib, torch, dev, sh, stream, peak, reps=50, warm=10):
+    """n = 2^30 (8 GiB per vector) split over 1, 2, 4, 8 streams: GB/s over
+    ``reps`` back-to-back calls (each 24 GiB, far larger than L2)."""
+    n = 1 << 30
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 3 * 8 * n + (2 << 30):
+        return {"skipped": f"needs {3 * 8 * n / 2**30:.0f} GiB free, have {free / 2**30:.0f}"}
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    w = torch.empty_like(x)
+    wx.wxpy_fill_uniform(x, 1, 1)
+    wx.wxpy_fill_uniform(y, 1, 2)
+    out = []
+    for s in (1, 2, 4, 8):
+        vid = wx.wxpy_variant_encode(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=0,
+                                     cache=1, carveout=-1, streams=s)
+        args = (vid, n, 0.5, x.data_ptr(), y.data_ptr(), w.data_ptr(), sh)
+        for _ in range(warm):
+            wx.check(lib.wxpy_run_variant(*args), "wxpy_run_variant")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lib.wxpy_run_variant(*args)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        gbs = BYTES_PER_ELEM * n / (t / 1e3) / 1e9
+        out.append({"streams": s, "ms_per_call": t, "gbs": gbs, "frac_of_peak": gbs / peak})
+    del x, y, w
+    torch.cuda.empty_cache()
+    return {"n": n, "reps": reps, "results": out}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-n sweep and stream-split measurements")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * wxpy.h -- C ABI of the GB300 (sm_103a) VecWXPY library.
+ *
+ * The operation.  For FP64 vectors x, y, w of length n and a scalar alpha,
+ *
+ *     w[i] = RN( RN(alpha * x[i]) + y[i] ),   i = 0 .. n-1,
+ *
+ * in IEEE-754 binary64, round-to-nearest-even, the product and the sum rounded
+ * separately (no fused multiply-add).  This is the PETSc vector kernel that the
+ * paper autotunes and names "vecwxpy" (Sec. 3, Fig. 1); the paper does not write
+ * the formula, and PETSc's VecWXPY defines it.  Every entry point of this file
+ * computes exactly these bits, whatever variant runs.
+ *
+ * The method.  Following Sec. 2, the kernel exists as a family of parameterised
+ * code variants; an empirical search runs them, checks their outputs against a
+ * plain reference variant, and keeps the fastest per size bucket.  The search
+ * knobs are those of Sec. 3 (threads per block, blocks per grid, number of
+ * asynchronous streams, L1 size, unroll factor) plus the vector width and the
+ * cache policy of the loads and stores.
+ *
+ * Conventions for every call:
+ *  - Return value: a wxpy_status (0 = success).  No exception or signal
+ *    crosses the ABI.  After WXPY_ECUDA, wxpy_last_cuda_error() and
+ *    wxpy_last_error_message() give details for the calling thread.
+ *  - Pointers named x, y, w, *_dev are DEVICE addresses on the current CUDA
+ *    device; the caller owns that memory.  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls documented "asynchronous" only enqueue work on it.
+ *  - Vector arguments must be 8-byte aligned.  Exact aliasing (w == x,
+ *    w == y, x == y) is allowed and defined element-wise: each element is
+ *    read before it is written.  Any partial overlap of w with x or y is
+ *    rejected with WXPY_EOVERLAP (x and y may overlap each other freely,
+ *    since both are only read).
+ */
+#ifndef WXPY_H
+#define WXPY_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef enum wxpy_status {
+    WXPY_OK = 0,
+    WXPY_EINVAL = 1,    /* bad argument: n < 0, null or unaligned pointer, bad id */
+    WXPY_EOVERLAP = 2,  /* w partially overlaps x or y */
+    WXPY_ENOMEM = 3,    /* a library-owned allocation failed */
+    WXPY_EBUDGET = 4,   /* request larger than the server's memory budget */
+    WXPY_ECUDA = 5,     /* a CUDA runtime call failed (see wxpy_last_cuda_error) */
+    WXPY_ETIMEOUT = 6,  /* a bounded wait ran out */
+    WXPY_ENOTFOUND = 7, /* unknown ticket / no such entry */
+    WXPY_EBUSY = 8,     /* resource in use (for example a server at its slot limit) */
+    WXPY_EMISMATCH = 9  /* a variant's output differed from the reference variant */
+} wxpy_status;
+
+/* Static English text of a status code; never NULL. */
+const char *wxpy_strerror(int status);
+
+/* The cudaError_t of the calling thread's last failed CUDA call (0 if none). */
+int wxpy_last_cuda_error(void);
+
+/* Detail text of the calling thread's last error ("" if none).  The pointer
+ * stays valid until the thread's next call into the library. */
+const char *wxpy_last_error_message(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int wxpy_version(void);
+
+/* ---- device --------------------------------------------------------------- */
+typedef struct wxpy_device_info {
+    char name[128];          /* cudaDeviceProp::name */
+    int32_t device;          /* device ordinal */
+    int32_t sm_count;        /* streaming multiprocessors (152 on GB300) */
+    int32_t cc_major, cc_minor;
+    int64_t l2_bytes;        /* L2 cache size */
+    int64_t global_bytes;    /* device memory size */
+    int32_t runtime_version; /* CUDA runtime the library was built against */
+    int32_t reserved;
+} wxpy_device_info;
+
+/* Fills *out for the current device.  Synchronous; no allocation. */
+int wxpy_device_query(wxpy_device_info *out);
+
+/* ---- classification (host only, no CUDA call) ------------------------------ */
+enum {
+    WXPY_ALIAS_XY = 1,  /* x == y: y is not loaded (16 bytes per element) */
+    WXPY_ALIAS_WX = 2,  /* w == x */
+    WXPY_ALIAS_WY = 4   /* w == y */
+};
+
+typedef struct wxpy_class_info {
+    int32_t alias;     /* OR of WXPY_ALIAS_* */
+    int32_t align;     /* widest vector width in bytes (32, 16 or 8) at which
+                          x, y and w share their offset */
+    int32_t head;      /* elements before w reaches `align` bytes (<= 3, <= n) */
+    int32_t bucket;    /* size bucket floor(log2 n); -1 when n == 0 */
+    int32_t tune_key;  /* index of the (bucket, align, alias group) cell of the
+                          tuning table, -1 when n == 0 */
+    int32_t reserved;
+} wxpy_class_info;
+
+/* Validates (n, x, y, w) exactly as wxpy() does and classifies the call:
+ * the step that picks the tuned variant (Sec. 2 selection is per size bucket
+ * here, and also per alignment and aliasing class).  Pure host arithmetic on
+ * the pointer values; never dereferences them. */
+int wxpy_classify(int64_t n, const double *x, const double *y, const double *w,
+                  wxpy_class_info *out);
+
+/* ---- the variant space (Sec. 2 variants, Sec. 3 knobs) --------------------- */
+typedef struct wxpy_variant_info {
+    int32_t id;            /* flat index in [0, wxpy_variant_count()), or -1 */
+    int32_t vec_bytes;     /* 8, 16, 32: width of each load and store */
+    int32_t unroll;        /* 1, 2, 4, 8: independent vectors per thread per pass */
+    int32_t threads;       /* threads per block: 128, 256, 512, 1024 */
+    int32_t blocks_per_sm; /* 0: one-shot grid (each thread makes one pass);
+                              k > 0: grid-stride loop over k * sm_count blocks */
+    int32_t cache;         /* 0: ld/st.global; 1: read-only path for the inputs
+                              (ld.global.nc.L1::no_allocate) and evict-first
+                              stores; 2: evict-first (.cs) loads and stores.
+                              1 becomes 2 when w aliases x or y. */
+    int32_t carveout;      /* -1: driver default; else the preferred shared
+                              memory carveout in percent (0, 50, 100): the
+                              rest of the unified L1/shared array is L1 */
+    int32_t streams;       /* 1, 2, 4, 8: the call is cut into this many
+                              256-byte-aligned pieces, each on its own stream,
+                              forked from and joined back into `stream` */
+} wxpy_variant_info;
+
+/* Number of variants in the space (vec_bytes x unroll x threads x grid mode x
+ * cache x carveout x streams). */
+int wxpy_variant_count(void);
+
+/* Decodes variant `id` into *out.  WXPY_EINVAL for an id out of range. */
+int wxpy_variant_describe(int id, wxpy_variant_info *out);
+
+/* Encodes *v into its flat id (written to *id).  WXPY_EINVAL if a field is
+ * not one of the listed values. */
+int wxpy_variant_encode(const wxpy_variant_info *v, int *id);
+
+/* Forces every later wxpy() call of the process to use variant `id`
+ * (tests, benchmarks); id = -1 restores the normal lookup (tuned entry, else
+ * the built-in default). */
+int wxpy_set_variant(int id);
+
+/* Reports in *out the variant that wxpy(n, ., x, y, w, .) would launch now,
+ * after the adjustments to the call's class (vec_bytes capped at the class's
+ * alignment, cache 1 -> 2 under aliasing).  `tuned` (may be NULL) receives 1 if
+ * it came from the tuning table, 2 if forced by wxpy_set_variant, 0 if the
+ * built-in default. */
+int wxpy_lookup(int64_t n, const double *x, const double *y, const double *w,
+                wxpy_variant_info *out, int *tuned);
+
+/* ---- the operation ----------------------------------------------------------- */
+
+/* w[i] = RN(RN(alpha*x[i]) + y[i]) for i in [0, n) (Sec. 3, Fig. 1 vecwxpy).
+ * Asynchronous on `stream`; allocates nothing; may be captured in a CUDA
+ * graph.  Runs the variant that wxpy_lookup() reports.  n == 0 is a no-op
+ * (pointers may then be NULL).  Errors: WXPY_EINVAL (n < 0, null or
+ * non-8-byte-aligned pointer), WXPY_EOVERLAP, WXPY_ECUDA (launch failed). */
+int wxpy(int64_t n, double alpha, const double *x, const double *y, double *w,
+         void *stream);
+
+/* The same operation with variant `id` (the tuner's and the tests' entry).
+ * The variant is adjusted to the call's class as described at wxpy_lookup. */
+int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,
+                     const double *y, double *w, void *stream);
+
+/* The plain reference variant of Sec. 2: one element per thread, scalar
+ * loads and stores, one-shot grid.  The tuner compares every candidate's
+ * output with this variant's, bit for bit. */
+int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
+                   double *w, void *stream);
+
+/* ---- seeded synthetic inputs ----------------------------------------------------- */
+
+/* Stream tags used by the library's own synthetic inputs (server requests). */
+enum { WXPY_TAG_X = 1, WXPY_TAG_Y = 2, WXPY_TAG_ALPHA = 3, WXPY_TAG_LEN = 4 };
+
+/* dst[i] = lo + (hi - lo) * u(start + i), i in [0, n), where u(k) =
+ * (b(k) >> 11) * 2^-53 and b(k) is output k of splitmix64 (Steele, Lea and
+ * Flood, OOPSLA 2014) seeded with the key of stream (seed, tag); that key is
+ * output number `tag` of splitmix64 seeded with `seed`.  Output k of the
+ * generator seeded with s is mix64(s + (k+1) * 0x9E3779B97F4A7C15).
+ * The paper has no counterpart: this only makes synthetic inputs (the server
+ * fills request vectors with it).  For (lo, hi) = (-1, 1) or (-2, 2) every
+ * value is exact, so a host implementation reproduces it bit for bit.
+ * Asynchronous on `stream`; dst is a device pointer, 8-byte aligned.
+ * WXPY_EINVAL for n < 0, start < 0, hi <= lo or a bad pointer. */
+int wxpy_fill_uniform(int64_t n, uint64_t seed, uint32_t tag, int64_t start,
+                      double lo, double hi, double *dst, void *stream);
+
+/* ---- fault injection for host-side failure tests ------------------------------ */
+
+/* The next `count` kernel launches made by the library fail with
+ * cudaError_t `cuda_error` (returned as WXPY_ECUDA) without touching the GPU.
+ * count = 0 clears it.  Process-wide. */
+int wxpy_debug_inject_launch_error(int cuda_error, int count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WXPY_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) VecWXPY: FP64 w = alpha*x + y as an autotuned CUDA kernel family.
+
+The paper (Sec. 2) tunes a kernel by generating annotated variants, running
+them, checking their outputs against the plain reference code and keeping the
+fastest; this package applies that method to the kernel it reports on
+(Sec. 3, Fig. 1, "vecwxpy").  The computation lives in ``libwxpy.so``
+(C ABI: ``include/wxpy.h``); this package is its ctypes binding.  Importing it
+does not load the library; the first call does, and raises if it is missing.
+"""
+from .binding import (  # noqa: F401
+    WxpyError, lib, check, version, strerror,
+    wxpy, wxpy_run_variant, wxpy_reference, wxpy_lookup, wxpy_classify,
+    wxpy_device_query, wxpy_variant_count, wxpy_variant_describe, wxpy_variant_encode,
+    wxpy_set_variant, wxpy_debug_inject_launch_error, wxpy_fill_uniform,
+    ALIAS_XY, ALIAS_WX, ALIAS_WY,
+    WXPY_OK, WXPY_EINVAL, WXPY_EOVERLAP, WXPY_ENOMEM, WXPY_EBUDGET, WXPY_ECUDA,
+    WXPY_ETIMEOUT, WXPY_ENOTFOUND, WXPY_EBUSY, WXPY_EMISMATCH,
+)

@@ -1,0 +1,240 @@
+"""ctypes binding of ``libwxpy.so`` (declared in ``include/wxpy.h``).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY = os.path.join(HERE, "libwxpy.so")
+
+WXPY_OK = 0
+WXPY_EINVAL = 1
+WXPY_EOVERLAP = 2
+WXPY_ENOMEM = 3
+WXPY_EBUDGET = 4
+WXPY_ECUDA = 5
+WXPY_ETIMEOUT = 6
+WXPY_ENOTFOUND = 7
+WXPY_EBUSY = 8
+WXPY_EMISMATCH = 9
+
+ALIAS_XY, ALIAS_WX, ALIAS_WY = 1, 2, 4
+
+
+class WxpyError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({strerror(status)}){': ' + detail if detail else ''}")
+
+
+class DeviceInfo(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 128), ("device", ctypes.c_int32),
+                ("sm_count", ctypes.c_int32), ("cc_major", ctypes.c_int32),
+                ("cc_minor", ctypes.c_int32), ("l2_bytes", ctypes.c_int64),
+                ("global_bytes", ctypes.c_int64), ("runtime_version", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ClassInfo(ctypes.Structure):
+    _fields_ = [("alias", ctypes.c_int32), ("align", ctypes.c_int32), ("head", ctypes.c_int32),
+                ("bucket", ctypes.c_int32), ("tune_key", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class VariantInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int32), ("vec_bytes", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("cache", ctypes.c_int32), ("carveout", ctypes.c_int32),
+                ("streams", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_INT = ctypes.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "wxpy_strerror": (ctypes.c_char_p, [_INT]),
+    "wxpy_last_cuda_error": (_INT, []),
+    "wxpy_last_error_message": (ctypes.c_char_p, []),
+    "wxpy_version": (_INT, []),
+    "wxpy_device_query": (_INT, [ctypes.POINTER(DeviceInfo)]),
+    "wxpy_classify": (_INT, [_I64, _P, _P, _P, ctypes.POINTER(ClassInfo)]),
+    "wxpy_variant_count": (_INT, []),
+    "wxpy_variant_describe": (_INT, [_INT, ctypes.POINTER(VariantInfo)]),
+    "wxpy_variant_encode": (_INT, [ctypes.POINTER(VariantInfo), ctypes.POINTER(_INT)]),
+    "wxpy_set_variant": (_INT, [_INT]),
+    "wxpy_lookup": (_INT, [_I64, _P, _P, _P, ctypes.POINTER(VariantInfo), ctypes.POINTER(_INT)]),
+    "wxpy": (_INT, [_I64, _D, _P, _P, _P, _P]),
+    "wxpy_run_variant": (_INT, [_INT, _I64, _D, _P, _P, _P, _P]),
+    "wxpy_reference": (_INT, [_I64, _D, _P, _P, _P, _P]),
+    "wxpy_debug_inject_launch_error": (_INT, [_INT, _INT]),
+    "wxpy_fill_uniform": (_INT, [_I64, ctypes.c_uint64, ctypes.c_uint32, _I64, _D, _D, _P, _P]),
+}
+
+_lock = threading.Lock()
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded ``libwxpy.so``; raises if it has not been built."""
+    global _lib_handle
+    with _lock:
+        if _lib_handle is None:
+            if not os.path.exists(LIBRARY):
+                raise RuntimeError(
+                    f"{LIBRARY} is not built; build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+            h = ctypes.CDLL(LIBRARY)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib_handle = h
+        return _lib_handle
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().wxpy_strerror(status).decode()
+    except Exception:  # the library may be the thing that is missing
+        return "?"
+
+
+def check(status: int, where: str) -> None:
+    if status != WXPY_OK:
+        detail = lib().wxpy_last_error_message().decode(errors="replace")
+        raise WxpyError(status, where, detail)
+
+
+# ---------------------------------------------------------------- marshalling
+def _stream_handle(stream) -> int | None:
+    """cudaStream_t of ``stream`` (torch.cuda.Stream, int or None = torch's current)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _vec(t, name: str):
+    """(n, device pointer) of a contiguous 1-D float64 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1):
+        raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    return t.numel(), t.data_ptr()
+
+
+# ---------------------------------------------------------------- API
+def version() -> int:
+    return lib().wxpy_version()
+
+
+def wxpy_device_query() -> dict:
+    info = DeviceInfo()
+    check(lib().wxpy_device_query(ctypes.byref(info)), "wxpy_device_query")
+    d = {f: getattr(info, f) for f, _ in info._fields_ if f != "reserved"}
+    d["name"] = info.name.decode()
+    return d
+
+
+def wxpy_classify(n: int, x: int, y: int, w: int) -> dict:
+    """Classification of a call from raw pointer values (host only)."""
+    info = ClassInfo()
+    check(lib().wxpy_classify(n, x, y, w, ctypes.byref(info)), "wxpy_classify")
+    return {f: getattr(info, f) for f, _ in info._fields_ if f != "reserved"}
+
+
+def wxpy_variant_count() -> int:
+    return lib().wxpy_variant_count()
+
+
+def wxpy_variant_describe(vid: int) -> dict:
+    info = VariantInfo()
+    check(lib().wxpy_variant_describe(vid, ctypes.byref(info)), "wxpy_variant_describe")
+    return info.as_dict()
+
+
+def wxpy_variant_encode(**fields) -> int:
+    info = VariantInfo(id=-1, **fields)
+    out = _INT()
+    check(lib().wxpy_variant_encode(ctypes.byref(info), ctypes.byref(out)), "wxpy_variant_encode")
+    return out.value
+
+
+def wxpy_set_variant(vid: int) -> None:
+    check(lib().wxpy_set_variant(vid), "wxpy_set_variant")
+
+
+def wxpy_lookup(x, y, w) -> tuple[dict, int]:
+    """(variant, source) that wxpy(., x, y, w) would run; source 0 default, 1 tuned, 2 forced."""
+    n, px = _vec(x, "x")
+    _, py = _vec(y, "y")
+    _, pw = _vec(w, "w")
+    info = VariantInfo()
+    src = _INT()
+    check(lib().wxpy_lookup(n, px, py, pw, ctypes.byref(info), ctypes.byref(src)), "wxpy_lookup")
+    return info.as_dict(), src.value
+
+
+def _prepare(alpha, x, y, w):
+    import torch
+    n, px = _vec(x, "x")
+    ny, py = _vec(y, "y")
+    if w is None:
+        w = torch.empty_like(x)
+    nw, pw = _vec(w, "w")
+    if not (n == ny == nw):
+        raise ValueError(f"length mismatch: x {n}, y {ny}, w {nw}")
+    return n, float(alpha), px, py, pw, w
+
+
+def wxpy(alpha: float, x, y, w=None, stream=None):
+    """w = alpha*x + y (FP64, no FMA) on ``stream``; returns w (allocated if None)."""
+    n, a, px, py, pw, w = _prepare(alpha, x, y, w)
+    check(lib().wxpy(n, a, px, py, pw, _stream_handle(stream)), "wxpy")
+    return w
+
+
+def wxpy_run_variant(vid: int, alpha: float, x, y, w=None, stream=None):
+    n, a, px, py, pw, w = _prepare(alpha, x, y, w)
+    check(lib().wxpy_run_variant(vid, n, a, px, py, pw, _stream_handle(stream)),
+          "wxpy_run_variant")
+    return w
+
+
+def wxpy_reference(alpha: float, x, y, w=None, stream=None):
+    n, a, px, py, pw, w = _prepare(alpha, x, y, w)
+    check(lib().wxpy_reference(n, a, px, py, pw, _stream_handle(stream)), "wxpy_reference")
+    return w
+
+
+def wxpy_fill_uniform(dst, seed: int, tag: int, lo: float = -1.0, hi: float = 1.0,
+                      start: int = 0, stream=None):
+    """Fill the float64 CUDA tensor ``dst`` from stream (seed, tag) starting at ``start``."""
+    n, p = _vec(dst, "dst")
+    check(lib().wxpy_fill_uniform(n, seed & ((1 << 64) - 1), tag, start, lo, hi, p,
+                                  _stream_handle(stream)), "wxpy_fill_uniform")
+    return dst
+
+
+def wxpy_debug_inject_launch_error(cuda_error: int, count: int) -> None:
+    check(lib().wxpy_debug_inject_launch_error(cuda_error, count),
+          "wxpy_debug_inject_launch_error")

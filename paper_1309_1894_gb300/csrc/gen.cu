@@ -1,0 +1,116 @@
+// gen.cu -- device-side seeded inputs and the bitwise comparison used by the tuner.
+//
+// The generator is splitmix64 (Steele, Lea & Flood, OOPSLA 2014), written here
+// from its published definition and used in counter form: output k of the
+// generator seeded with s is mix64(s + (k+1)*0x9E3779B97F4A7C15).  A stream
+// (seed, tag) is keyed by output number `tag` of the generator seeded with
+// `seed`; element i of the stream is output number i of the generator seeded
+// with that key.  A double u = (bits >> 11) * 2^-53 is uniform on [0, 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace wx {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t stream_key(uint64_t seed, uint32_t tag) {
+    return mix64(seed + ((uint64_t)tag + 1) * kGolden);
+}
+
+// dst[i] = lo + width * u(start + i).  lo + width*u is computed as two
+// correctly rounded operations; for the ranges the library uses (width a power
+// of two, lo = -width/2) every step is exact.
+__global__ void fill_uniform_kernel(double *dst, int64_t n, uint64_t key, int64_t start,
+                                    double lo, double width) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t b = mix64(key + (uint64_t)(start + i + 1) * kGolden);
+        const double u = (double)(b >> 11) * 0x1.0p-53;
+        dst[i] = __dadd_rn(lo, __dmul_rn(width, u));
+    }
+}
+
+// count += number of i with bits(a[i]) != bits(b[i]).
+__global__ void count_mismatch_kernel(const uint64_t *a, const uint64_t *b, int64_t n,
+                                      unsigned long long *count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        local += (a[i] != b[i]) ? 1ull : 0ull;
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_down_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+// Reads `n` words and folds them into *sink: evicts the L2 between timed runs
+// without leaving dirty lines behind.
+__global__ void l2_flush_kernel(const uint64_t *buf, int64_t n, uint64_t *sink) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint64_t acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        acc ^= buf[i];
+    if (acc == 0x5eedf00d5eedf00dull) *sink = acc;  // practically never; keeps the loads
+}
+
+int launch_fill_uniform(double *dst, int64_t n, uint64_t seed, uint32_t tag, int64_t start,
+                        double lo, double hi, cudaStream_t s) {
+    if (n == 0) return WXPY_OK;
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)dp->sm_count * 8);
+    cudaError_t e = injected_launch_error();
+    if (e == cudaSuccess) {
+        fill_uniform_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, stream_key(seed, tag), start,
+                                                             lo, hi - lo);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "fill kernel launch");
+    return WXPY_OK;
+}
+
+int launch_count_mismatch(const double *a, const double *b, int64_t n,
+                          unsigned long long *count_dev, cudaStream_t s) {
+    if (n == 0) return WXPY_OK;
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)dp->sm_count * 4);
+    count_mismatch_kernel<<<(unsigned)blocks, 256, 0, s>>>((const uint64_t *)a,
+                                                          (const uint64_t *)b, n, count_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "compare kernel launch");
+    return WXPY_OK;
+}
+
+int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s) {
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    l2_flush_kernel<<<(unsigned)dp->sm_count * 4, 512, 0, s>>>((const uint64_t *)buf, bytes / 8,
+                                                              (uint64_t *)sink);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "l2 flush launch");
+    return WXPY_OK;
+}
+
+}  // namespace wx
+
+using namespace wx;
+
+extern "C" int wxpy_fill_uniform(int64_t n, uint64_t seed, uint32_t tag, int64_t start, double lo,
+                                 double hi, double *dst, void *stream) {
+    if (n < 0 || start < 0) return fail(WXPY_EINVAL, "negative n or start");
+    if (n > 0 && (!dst || ((uintptr_t)dst & 7u))) return fail(WXPY_EINVAL, "bad destination");
+    if (!(hi > lo)) return fail(WXPY_EINVAL, "need hi > lo");
+    return launch_fill_uniform(dst, n, seed, tag, start, lo, hi, (cudaStream_t)stream);
+}

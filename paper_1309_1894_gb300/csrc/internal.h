@@ -1,0 +1,89 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "wxpy.h"
+#include "single_kernel.cuh"
+
+namespace wx {
+
+// ---- errors (thread-local detail, see wxpy_last_error_message) ----
+int fail(int status, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail_cuda(cudaError_t e, const char *what);
+void clear_error();
+
+// ---- device properties, cached per ordinal ----
+struct DeviceProps {
+    int device = -1;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    int64_t l2_bytes = 0;
+    int64_t global_bytes = 0;
+    char name[128] = {0};
+};
+// Properties of the current device; nullptr (and the error recorded) on failure.
+const DeviceProps *current_device(int *status);
+
+// ---- the variant space ----
+struct Variant {
+    int vec_bytes, unroll, threads, blocks_per_sm, cache, carveout, streams;
+};
+constexpr int kVecBytes[3] = {8, 16, 32};
+constexpr int kUnroll[4] = {1, 2, 4, 8};
+constexpr int kThreads[4] = {128, 256, 512, 1024};
+constexpr int kBlocksPerSm[5] = {0, 1, 2, 4, 8};
+constexpr int kCache[3] = {0, 1, 2};
+constexpr int kCarveout[4] = {-1, 0, 50, 100};
+constexpr int kStreams[4] = {1, 2, 4, 8};
+constexpr int kVariantCount = 3 * 4 * 4 * 5 * 3 * 4 * 4;
+
+bool decode_variant(int id, Variant *v);
+int encode_variant(const Variant &v);  // -1 if a field is out of the space
+void to_info(const Variant &v, int id, wxpy_variant_info *out);
+
+// ---- classification ----
+struct CallClass {
+    int alias;      // WXPY_ALIAS_* bits
+    int align;      // 32, 16, 8
+    int head;       // for `align`
+    int bucket;     // floor(log2 n) or -1
+    int tune_key;   // -1 when n == 0
+};
+int classify(int64_t n, const double *x, const double *y, const double *w, CallClass *c);
+constexpr int kBuckets = 64;
+constexpr int kTuneKeys = kBuckets * 3 * 4;
+int tune_key_of(int bucket, int align, int alias);
+
+// The variant after adjustment to a call class (width cap, cache under aliasing).
+Variant adjust_variant(const Variant &v, const CallClass &c);
+// Built-in default when nothing is tuned or forced.
+Variant default_variant(const CallClass &c, int64_t n);
+
+// Tuning table (flat variant ids, -1 = none) and the forced id.
+extern std::atomic<int> g_forced_variant;
+extern std::atomic<int> g_tuned[kTuneKeys];
+
+// ---- launching ----
+// Runs the (already adjusted) variant on stream s.  Handles the stream split.
+int run_variant(const Variant &v, const CallClass &c, int64_t n, double alpha,
+                const double *x, const double *y, double *w, cudaStream_t s);
+// Launch gate for fault injection: returns cudaSuccess or the injected error.
+cudaError_t injected_launch_error();
+
+// gen.cu: seeded device inputs, bitwise comparison, L2 eviction.
+uint64_t stream_key(uint64_t seed, uint32_t tag);
+int launch_fill_uniform(double *dst, int64_t n, uint64_t seed, uint32_t tag, int64_t start,
+                        double lo, double hi, cudaStream_t s);
+int launch_count_mismatch(const double *a, const double *b, int64_t n,
+                          unsigned long long *count_dev, cudaStream_t s);
+int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s);
+
+cudaError_t launch_reference(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s);
+SingleEntry single_entry(int vw, int unroll, int gs, int cache, int xy);
+
+}  // namespace wx

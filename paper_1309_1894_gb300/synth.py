@@ -96,6 +96,20 @@ def uniform_pm2(seed: int, tag: int, count: int, start: int = 0) -> np.ndarray:
     return 4.0 * u01(seed, tag, start, count) - 2.0
 
 
+def bits_at(seed: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """Raw outputs of stream (seed, tag) at arbitrary indices ``idx``."""
+    key = np.uint64(stream_key(seed, tag))
+    with np.errstate(over="ignore"):
+        z = key + (np.asarray(idx).astype(np.uint64) + np.uint64(1)) * np.uint64(GOLDEN)
+    return _mix64_array(z)
+
+
+def uniform_pm1_at(seed: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """U(-1, 1) values of stream (seed, tag) at arbitrary indices ``idx``."""
+    b = bits_at(seed, tag, idx) >> np.uint64(11)
+    return 2.0 * (b.astype(np.float64) * (2.0 ** -53)) - 1.0
+
+
 def alpha_scalar(seed: int, index: int = 0) -> float:
     """One alpha ~ U(-2, 2) from stream TAG_ALPHA at ``index``."""
     return float(uniform_pm2(seed, TAG_ALPHA, 1, start=index)[0])

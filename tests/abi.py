@@ -1,0 +1,20 @@
+"""Helpers to read the C ABI declared under include/ (used by the ABI tests)."""
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/*.h (comments stripped)."""
+    names = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        with open(path) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        src = re.sub(r"#[^\n]*", " ", src)
+        for m in re.finditer(r"\b(wxpy\w*)\s*\(", src):
+            names.append(m.group(1))
+    return sorted(set(names))

@@ -1,0 +1,143 @@
+"""The C ABI library (no GPU): it builds, loads, exports every declared symbol,
+and its host-side logic (validation, classification, variant space) is right.
+No call here launches a kernel."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import abi
+import paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import binding
+from paper_1309_1894_gb300 import build as wbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(wbuild.LIBRARY):
+        wbuild.build()
+    return wx.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = abi.declared_functions()
+    assert "wxpy" in names and len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", wbuild.LIBRARY],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in names:
+        getattr(lib, n)  # resolvable through dlsym too
+
+
+def test_binding_covers_every_symbol():
+    names = set(abi.declared_functions())
+    bound = set(binding.SIGNATURES)
+    assert names <= bound, f"not bound in Python: {sorted(names - bound)}"
+
+
+def test_strerror(lib):
+    for s in range(10):
+        assert wx.strerror(s) and wx.strerror(s) != "unknown status"
+    assert wx.strerror(99) == "unknown status"
+
+
+def test_variant_space_roundtrip(lib):
+    count = wx.wxpy_variant_count()
+    assert count == 3 * 4 * 4 * 5 * 3 * 4 * 4
+    seen = set()
+    for vid in range(0, count, 7):
+        d = wx.wxpy_variant_describe(vid)
+        assert d["id"] == vid
+        fields = {k: v for k, v in d.items() if k != "id"}
+        assert wx.wxpy_variant_encode(**fields) == vid
+        seen.add(tuple(fields.values()))
+    assert len(seen) == len(range(0, count, 7))
+    with pytest.raises(wx.WxpyError):
+        wx.wxpy_variant_describe(count)
+    with pytest.raises(wx.WxpyError):
+        wx.wxpy_variant_describe(-1)
+    with pytest.raises(wx.WxpyError):
+        wx.wxpy_variant_encode(vec_bytes=24, unroll=1, threads=128, blocks_per_sm=0,
+                               cache=0, carveout=-1, streams=1)
+
+
+BASE = 1 << 40  # a pointer value; never dereferenced by wxpy_classify
+
+
+@pytest.mark.parametrize("off", [0, 8, 16, 24])
+def test_classify_coaligned(lib, off):
+    n = 1000
+    c = wx.wxpy_classify(n, BASE + off, BASE + 65536 + off, BASE + 2 * 65536 + off)
+    assert c["align"] == 32 and c["alias"] == 0
+    assert c["head"] == ((32 - off) % 32) // 8
+    assert c["bucket"] == 9
+
+
+def test_classify_mixed_alignment(lib):
+    n = 100
+    assert wx.wxpy_classify(n, BASE + 0, BASE + 65536 + 16, BASE + 2 * 65536)["align"] == 16
+    assert wx.wxpy_classify(n, BASE + 0, BASE + 65536 + 8, BASE + 2 * 65536 + 24)["align"] == 8
+    assert wx.wxpy_classify(n, BASE + 8, BASE + 65536 + 8, BASE + 2 * 65536 + 24)["align"] == 16
+
+
+def test_classify_aliasing(lib):
+    n = 64
+    x, y, w = BASE, BASE + 4096, BASE + 8192
+    assert wx.wxpy_classify(n, x, y, x)["alias"] == wx.ALIAS_WX
+    assert wx.wxpy_classify(n, x, y, y)["alias"] == wx.ALIAS_WY
+    assert wx.wxpy_classify(n, x, x, w)["alias"] == wx.ALIAS_XY
+    assert wx.wxpy_classify(n, x, x, x)["alias"] == wx.ALIAS_XY | wx.ALIAS_WX | wx.ALIAS_WY
+    # x and y may overlap partially: both are only read
+    assert wx.wxpy_classify(n, x, x + 8, w)["alias"] == 0
+
+
+def test_classify_buckets(lib):
+    for k in range(0, 40):
+        for n in (1 << k, (1 << k) + 3):
+            if n >= (1 << (k + 1)):
+                continue
+            assert wx.wxpy_classify(n, BASE, BASE + (1 << 44), BASE + (2 << 44))["bucket"] == k
+    # 2^k and 2^k + 3 share a bucket (k >= 2)
+    assert wx.wxpy_classify(0, 0, 0, 0)["bucket"] == -1
+
+
+@pytest.mark.parametrize("args,status", [
+    ((-1, BASE, BASE + 4096, BASE + 8192), wx.WXPY_EINVAL),
+    ((10, 0, BASE + 4096, BASE + 8192), wx.WXPY_EINVAL),
+    ((10, BASE, 0, BASE + 8192), wx.WXPY_EINVAL),
+    ((10, BASE, BASE + 4096, 0), wx.WXPY_EINVAL),
+    ((10, BASE + 4, BASE + 4096, BASE + 8192), wx.WXPY_EINVAL),
+    ((10, BASE, BASE + 4096, BASE + 8), wx.WXPY_EOVERLAP),
+    ((10, BASE, BASE + 4096, BASE + 4096 - 8), wx.WXPY_EOVERLAP),
+    ((10, BASE, BASE + 4096, BASE + 4096 + 72), wx.WXPY_EOVERLAP),
+])
+def test_validation_errors(lib, args, status):
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy_classify(*args)
+    assert e.value.status == status
+    # the launching entry points reject the same arguments before any CUDA call
+    n, x, y, w = args
+    assert lib.wxpy(n, 1.0, x, y, w, None) == status
+    assert lib.wxpy_run_variant(0, n, 1.0, x, y, w, None) == status
+
+
+def test_empty_call_is_a_noop_without_cuda(lib):
+    assert lib.wxpy(0, 1.0, None, None, None, None) == 0
+    assert lib.wxpy_run_variant(5, 0, 1.0, None, None, None, None) == 0
+    assert lib.wxpy_reference(0, 1.0, None, None, None, None) == 0
+
+
+def test_error_message_is_thread_local_text(lib):
+    assert lib.wxpy(-5, 1.0, None, None, None, None) == wx.WXPY_EINVAL
+    msg = lib.wxpy_last_error_message().decode()
+    assert "negative" in msg
+
+
+def test_set_variant_range(lib):
+    with pytest.raises(wx.WxpyError):
+        wx.wxpy_set_variant(wx.wxpy_variant_count())
+    wx.wxpy_set_variant(3)
+    wx.wxpy_set_variant(-1)

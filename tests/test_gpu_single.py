@@ -1,0 +1,281 @@
+"""GPU parity of the single-call path through the C ABI: bitwise against the oracle.
+
+The method (paper Sec. 2) accepts a variant only if its outputs equal the
+reference results; here every variant family member, every alias class, every
+alignment offset and ragged sizes are compared with the CPU oracle bit for bit
+(w = RN(RN(alpha*x)+y), Sec. 3 / Fig. 1 vecwxpy), and guard canaries around
+each buffer must stay untouched.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import synth
+from gpu_util import Guarded, bits_equal, dev_bits_equal
+
+pytestmark = pytest.mark.gpu
+
+ALIASES = ["none", "w=x", "w=y", "x=y", "w=x=y"]
+
+
+def make_case(n, off, alias, seed, offs=None):
+    """Device vectors (x, y, w) for one case, their host inputs and the expected w."""
+    alpha, xh, yh = synth.vectors(seed, n)
+    ox, oy, ow = offs if offs is not None else (off, off, off)
+    gx = Guarded(n, ox).set(xh)
+    gy = Guarded(n, oy).set(yh)
+    gw = Guarded(n, ow)
+    x, y, w = gx.t, gy.t, gw.t
+    guards = [gx, gy, gw]
+    if alias == "w=x":
+        w, guards = x, [gx, gy]
+        want = oracle.wxpy(alpha, xh, yh)
+    elif alias == "w=y":
+        w, guards = y, [gx, gy]
+        want = oracle.wxpy(alpha, xh, yh)
+    elif alias == "x=y":
+        y, guards = x, [gx, gw]
+        want = oracle.wxpy(alpha, xh, xh)
+    elif alias == "w=x=y":
+        y, w, guards = x, x, [gx]
+        want = oracle.wxpy(alpha, xh, xh)
+    else:
+        want = oracle.wxpy(alpha, xh, yh)
+    return alpha, (x, y, w), (xh, yh), want, guards
+
+
+def restore(alias, x, y, xh, yh):
+    """Reset inputs that an in-place call overwrote."""
+    if alias in ("w=x", "x=y", "w=x=y"):
+        x.copy_(torch.from_numpy(xh))
+    if alias == "w=y":
+        y.copy_(torch.from_numpy(yh))
+
+
+def covering_variants():
+    """Every (vec, unroll, grid mode, cache) at 256 threads, plus every block
+    size, carveout and stream count."""
+    enc = wx.wxpy_variant_encode
+    vs = []
+    for vb in (8, 16, 32):
+        for u in (1, 2, 4, 8):
+            for bps in (0, 1, 8):
+                for c in (0, 1, 2):
+                    vs.append(enc(vec_bytes=vb, unroll=u, threads=256, blocks_per_sm=bps,
+                                  cache=c, carveout=-1, streams=1))
+    for t in (128, 512, 1024):
+        for u in (1, 8):
+            vs.append(enc(vec_bytes=32, unroll=u, threads=t, blocks_per_sm=2, cache=1,
+                          carveout=-1, streams=1))
+    for co in (0, 50, 100):
+        vs.append(enc(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=0, cache=1,
+                      carveout=co, streams=1))
+    for s in (2, 4, 8):
+        vs.append(enc(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=4, cache=1,
+                      carveout=-1, streams=s))
+    return vs
+
+
+@pytest.fixture(autouse=True)
+def _reset_forced():
+    wx.wxpy_set_variant(-1)
+    yield
+    wx.wxpy_set_variant(-1)
+
+
+def test_device_generator_matches_host():
+    for (lo, hi, host) in ((-1.0, 1.0, synth.uniform_pm1), (-2.0, 2.0, synth.uniform_pm2)):
+        d = torch.empty(100003, dtype=torch.float64, device="cuda")
+        wx.wxpy_fill_uniform(d, seed=synth.BASE_SEED, tag=synth.TAG_X, lo=lo, hi=hi, start=12345)
+        ok, msg = bits_equal(d, host(synth.BASE_SEED, synth.TAG_X, 100003, start=12345))
+        assert ok, msg
+
+
+@pytest.mark.parametrize("alias", ALIASES)
+@pytest.mark.parametrize("off", [0, 8, 24])
+def test_every_variant_family_member(alias, off):
+    vids = covering_variants()
+    for n in (1, 5, 67, 4099, 262147, 600005):
+        alpha, (x, y, w), (xh, yh), want, guards = make_case(n, off, alias, 1000 + n)
+        want_d = torch.from_numpy(want).cuda()
+        for vid in vids:
+            restore(alias, x, y, xh, yh)
+            wx.wxpy_run_variant(vid, alpha, x, y, w)
+            torch.cuda.synchronize()
+            assert dev_bits_equal(w, want_d), (
+                f"variant {wx.wxpy_variant_describe(vid)} n={n} off={off} alias={alias}: "
+                + bits_equal(w, want)[1])
+        for g in guards:
+            g.check()
+
+
+@pytest.mark.parametrize("alias", ALIASES)
+def test_tiny_sizes_exhaustive(alias):
+    """n = 0..67 at every 8-byte offset, default lookup and reference variant."""
+    for off in (0, 8, 16, 24):
+        for n in range(68):
+            alpha, (x, y, w), (xh, yh), want, guards = make_case(n, off, alias, 77 + n)
+            wx.wxpy(alpha, x, y, w)
+            torch.cuda.synchronize()
+            ok, msg = bits_equal(w, want)
+            assert ok, f"n={n} off={off} {msg}"
+            restore(alias, x, y, xh, yh)
+            wx.wxpy_reference(alpha, x, y, w)
+            torch.cuda.synchronize()
+            ok, msg = bits_equal(w, want)
+            assert ok, f"reference n={n} off={off} {msg}"
+            for g in guards:
+                g.check()
+
+
+@pytest.mark.parametrize("offs", [(0, 8, 24), (8, 0, 24), (24, 8, 0), (0, 16, 8), (16, 0, 0),
+                                  (8, 8, 24), (0, 0, 8)])
+def test_mixed_offsets(offs):
+    vids = covering_variants()[::5]
+    for n in (3, 1001, 70001):
+        alpha, (x, y, w), _, want, guards = make_case(n, 0, "none", 5 + n, offs=offs)
+        want_d = torch.from_numpy(want).cuda()
+        for vid in [None] + vids:
+            w.zero_()
+            if vid is None:
+                wx.wxpy(alpha, x, y, w)
+            else:
+                wx.wxpy_run_variant(vid, alpha, x, y, w)
+            torch.cuda.synchronize()
+            assert dev_bits_equal(w, want_d), f"offs={offs} n={n} vid={vid}"
+        for g in guards:
+            g.check()
+
+
+def test_size_sweep_default_lookup():
+    """n = 2^k and 2^k + 3, k = 10..22, offsets 0/8/24, against the oracle (full compare)."""
+    for k in range(10, 23):
+        for n in (1 << k, (1 << k) + 3):
+            for off in (0, 8, 24):
+                alpha, (x, y, w), _, want, guards = make_case(n, off, "none", k * 10 + off)
+                wx.wxpy(alpha, x, y, w)
+                torch.cuda.synchronize()
+                ok, msg = bits_equal(w, want)
+                assert ok, f"n={n} off={off}: {msg}"
+                for g in guards:
+                    g.check()
+
+
+def sampled_check(n, alpha, x, y, w, seed, xy_same=False, samples=200000):
+    """Compare w at sampled indices (plus both ends) with the oracle on the same
+    inputs, regenerated on the host from the counter-based generator."""
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([np.arange(min(n, 4096)),
+                                    np.arange(max(0, n - 4096), n),
+                                    rng.integers(0, n, samples)]))
+    xs = _values_at(seed, synth.TAG_X, idx)
+    ys = xs if xy_same else _values_at(seed, synth.TAG_Y, idx)
+    want = oracle.wxpy(alpha, xs, ys)
+    got = w[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), \
+        f"{int(np.sum(got.view(np.uint64) != want.view(np.uint64)))} sampled mismatches"
+
+
+def _values_at(seed, tag, idx):
+    """U(-1,1) values of stream (seed, tag) at arbitrary indices (counter-based access)."""
+    return synth.uniform_pm1_at(seed, tag, idx)
+
+
+@pytest.mark.parametrize("n", [(1 << 24) + 3, (1 << 28) + 3])
+def test_full_size_sampled(n):
+    """The sizes the benchmark times, in its launch configuration (default lookup)."""
+    seed = synth.BASE_SEED + 2
+    alpha = synth.alpha_scalar(seed)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    w = torch.full_like(x, float("nan"))
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    wx.wxpy(alpha, x, y, w)
+    torch.cuda.synchronize()
+    assert not bool(torch.isnan(w).any())
+    sampled_check(n, alpha, x, y, w, seed)
+    del x, y, w
+    torch.cuda.empty_cache()
+
+
+def test_large_split_streams_sampled():
+    """n = 2^30 (8 GiB per vector) through the 8-stream split, sampled."""
+    n = 1 << 30
+    seed = synth.BASE_SEED + 4
+    alpha = synth.alpha_scalar(seed)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    w = torch.full_like(x, float("nan"))
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    vid = wx.wxpy_variant_encode(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=0,
+                                 cache=1, carveout=-1, streams=8)
+    wx.wxpy_run_variant(vid, alpha, x, y, w)
+    torch.cuda.synchronize()
+    assert not bool(torch.isnan(w).any())
+    sampled_check(n, alpha, x, y, w, seed, samples=100000)
+    del x, y, w
+    torch.cuda.empty_cache()
+
+
+def test_non_default_stream_and_graph_capture():
+    n = 300001
+    alpha, (x, y, w), _, want, guards = make_case(n, 8, "none", 4242)
+    want_d = torch.from_numpy(want).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        wx.wxpy(alpha, x, y, w)
+    s.synchronize()
+    assert dev_bits_equal(w, want_d)
+    # capture a split variant (fork/join across internal streams) in a CUDA graph
+    vid = wx.wxpy_variant_encode(vec_bytes=32, unroll=2, threads=512, blocks_per_sm=0,
+                                 cache=1, carveout=-1, streams=4)
+    w.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        wx.wxpy_run_variant(vid, alpha, x, y, w)
+    for _ in range(3):
+        w.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert dev_bits_equal(w, want_d)
+    for gd in guards:
+        gd.check()
+
+
+def test_injected_launch_error_is_reported_and_cleared():
+    n = 1000
+    alpha, (x, y, w), _, want, _ = make_case(n, 0, "none", 9)
+    wx.wxpy_debug_inject_launch_error(719, 1)  # cudaErrorLaunchFailure
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy(alpha, x, y, w)
+    assert e.value.status == wx.WXPY_ECUDA
+    assert wx.lib().wxpy_last_cuda_error() == 719
+    wx.wxpy(alpha, x, y, w)  # the next call is not affected
+    torch.cuda.synchronize()
+    assert bits_equal(w, want)[0]
+    wx.wxpy_debug_inject_launch_error(0, 0)
+
+
+def test_lookup_reports_adjusted_variant():
+    n = 1000
+    _, (x, y, w), _, _, _ = make_case(n, 8, "none", 1, offs=(0, 8, 8))
+    v, src = wx.wxpy_lookup(x, y, w)
+    assert src == 0 and v["vec_bytes"] == 8
+    _, (x, y, w), _, _, _ = make_case(n, 0, "w=x", 1)
+    v, src = wx.wxpy_lookup(x, y, w)
+    assert v["cache"] != 1
+    wx.wxpy_set_variant(5)
+    v, src = wx.wxpy_lookup(x, y, w)
+    assert src == 2
+
+
+def test_device_query():
+    d = wx.wxpy_device_query()
+    assert d["sm_count"] > 0 and d["l2_bytes"] > 0
+    assert (d["cc_major"], d["cc_minor"]) >= (10, 0)
