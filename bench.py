@@ -315,6 +315,10 @@ def run_ours(args):
     cargs = [(n, px + 8 * o, py + 8 * o, pw + 8 * o) for (n, o) in calls]
     step_bytes = sum(BYTES_PER_ELEM * n for n, _ in calls)
 
+    # The method: one empirical search per size bucket of the sweep (or the
+    # cells of a saved tune cache), before anything is timed.
+    tuning = tune_buckets(wx, args, torch)
+
     # launches per call: the variant wxpy() runs, after the stream-split rule
     launches_per_step = 0
     variants = {}
@@ -385,6 +389,7 @@ def run_ours(args):
                      "peak_source": f"{peak_src} hbm_gbs",
                      "frac_of_nominal_8TBs": achieved / 8000.0},
         "gpu_launches": launches_per_step * K,
+        "tuning": tuning,
     }
     result["clocks"] = clocks.summary()
 
@@ -411,9 +416,36 @@ def run_ours(args):
     return 0
 
 
+def tune_buckets(wx, args, torch):
+    """Run wxpy_tune for every bucket of the sweep (n = 2^k), or load the cells
+    from --tune-cache when that file exists; returns a summary."""
+    t0 = time.perf_counter()
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        wx.wxpy_tune_cache_load(args.tune_cache, check_device=True)
+        return {"source": f"loaded {os.path.basename(args.tune_cache)}",
+                "seconds": time.perf_counter() - t0}
+    if args.no_tune:
+        return {"source": "built-in default variant (tuning skipped)"}
+    rows = []
+    for k in SWEEP_K:
+        r = wx.wxpy_tune(1 << k, 0)
+        rows.append({"k": k, "variant": r["best"], "us": r["best_us"],
+                     "default_us": r["default_us"], "reference_us": r["reference_us"],
+                     "gbs": r["best_gbs"], "candidates": r["candidates"],
+                     "rejected": r["rejected"]})
+    torch.cuda.synchronize()
+    if args.tune_cache:
+        wx.wxpy_tune_cache_save(args.tune_cache)
+    return {"source": "wxpy_tune per bucket (L2 flushed, median timing, bitwise check "
+                      "against the reference variant)",
+            "seconds": time.perf_counter() - t0, "buckets": rows}
+
+
 def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=9):
     """GB/s per n: median of ``reps`` with the L2 flushed (read of a 512 MB buffer)
-    before each timed call, and L2-resident (back-to-back) for n <= 2^22."""
+    before each timed call, and L2-resident (back-to-back) for n <= 2^22.  A
+    device sleep is queued ahead of each timed call so that the host's launch
+    latency is not part of the device time."""
     flush = torch.empty(64 << 20, dtype=torch.float64, device=x.device)
     flush.fill_(1.0)
     out = []
@@ -423,6 +455,7 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
         tf = []
         for _ in range(reps):
             flush.sum()
+            torch.cuda._sleep(100000)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -438,6 +471,7 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             lib.wxpy(*args)
+            torch.cuda._sleep(2000000)
             e0.record(stream)
             for _ in range(r):
                 lib.wxpy(*args)
@@ -539,10 +573,45 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-n sweep and stream-split measurements")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="time the built-in default variant instead of tuning first")
+    ap.add_argument("--tune-cache", default=None,
+                    help="load the tuned cells from this file if it exists, else tune and save")
+    ap.add_argument("--single", type=int, default=0,
+                    help="profiling mode: only run wxpy() on n = SINGLE, --reps times")
+    ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.single:
+        return run_single(args)
     return run_ours(args)
+
+
+def run_single(args):
+    """A small fixed case for ncu captures: n = args.single, inputs from the
+    device generator, the tuned (or default) variant, args.reps calls."""
+    import torch
+    import paper_1309_1894_gb300 as wx
+    from paper_1309_1894_gb300 import synth
+    n = args.single
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    w = torch.empty_like(x)
+    wx.wxpy_fill_uniform(x, synth.BASE_SEED, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, synth.BASE_SEED, synth.TAG_Y)
+    tuning = None
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        wx.wxpy_tune_cache_load(args.tune_cache, check_device=True)
+    elif not args.no_tune:
+        tuning = wx.wxpy_tune(n, 0)
+    v, src = wx.wxpy_lookup(x, y, w)
+    for _ in range(args.reps):
+        wx.wxpy(0.75, x, y, w)
+    torch.cuda.synchronize()
+    print(json.dumps({"single": n, "reps": args.reps, "variant": v, "source": src,
+                      "tuning": tuning}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -174,6 +174,66 @@ int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,
 int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
                    double *w, void *stream);
 
+/* ---- the empirical search (Sec. 2) and its persisted results ------------------ */
+
+/* Which call class wxpy_tune() reproduces (default: x, y, w 32-byte co-aligned
+ * and distinct), and how it searches. */
+enum {
+    WXPY_TUNE_ALIGN16 = 1 << 0,  /* x, y, w share their offset mod 16 bytes only */
+    WXPY_TUNE_ALIGN8 = 1 << 1,   /* ... mod 8 bytes only */
+    WXPY_TUNE_XY = 1 << 2,       /* x == y */
+    WXPY_TUNE_WALIAS = 1 << 3,   /* w == x (in-place update) */
+    WXPY_TUNE_QUICK = 1 << 4,    /* only the width x unroll x cache stage, fewer reps */
+    WXPY_TUNE_RESIDENT = 1 << 5  /* time back-to-back (L2-resident) runs instead of
+                                    flushing the L2 before every timed run */
+};
+
+typedef struct wxpy_tune_result {
+    wxpy_variant_info best;  /* the variant stored for the cell */
+    double best_us;          /* its median device time for n elements */
+    double default_us;       /* median time of the built-in default variant */
+    double reference_us;     /* median time of the plain reference variant */
+    double best_gbs;         /* algorithmic GB/s of `best` (24 bytes per element,
+                                16 when x == y) */
+    int32_t candidates;      /* variants run */
+    int32_t rejected;        /* variants whose output differed from the reference */
+    int32_t bucket;          /* floor(log2 n) */
+    int32_t tune_key;        /* the cell written */
+} wxpy_tune_result;
+
+/* Runs the search of Sec. 2 for the cell of size bucket floor(log2 n) and the
+ * class selected by `flags`: it allocates its own scratch (about 4 * 8n bytes
+ * plus a buffer of twice the L2 size), fills the inputs from the seeded
+ * generator, runs the reference variant once, then runs every candidate
+ * (coordinate search: width x unroll x cache, then threads x grid mode, then
+ * carveout x streams), rejects any whose output differs from the reference
+ * results by a single bit, times the rest with CUDA events (median of several
+ * runs, L2 flushed before each), and stores the fastest -- or the default
+ * variant, if it re-times faster -- in the tuning table, where every later
+ * wxpy() call of that cell finds it.  Synchronous; serialised by a mutex;
+ * frees its scratch before returning.  `out` may be NULL.
+ * Errors: WXPY_EINVAL (n <= 0, XY with WALIAS), WXPY_ENOMEM, WXPY_ECUDA,
+ * WXPY_EMISMATCH (no candidate matched the reference). */
+int wxpy_tune(int64_t n, unsigned flags, wxpy_tune_result *out);
+
+/* The tuning table: one variant id per cell (tune_key of wxpy_class_info),
+ * -1 for an untuned cell.  get/set/clear touch no device. */
+int wxpy_tune_get(int tune_key, int *variant_id);
+int wxpy_tune_set(int tune_key, int variant_id);
+int wxpy_tune_clear(void);
+
+/* Writes the tuned cells to a JSON file keyed by the device (name, compute
+ * capability, SM count, CUDA runtime): the selected variants of Sec. 2 kept
+ * across processes.  Replaces the file atomically. */
+int wxpy_tune_cache_save(const char *path);
+
+/* Reads a file written by wxpy_tune_cache_save and stores its cells.  With
+ * check_device != 0 a file tuned on another device is rejected (WXPY_EINVAL)
+ * and nothing is stored; a malformed file stores nothing either.  When the
+ * environment variable WXPY_TUNE_CACHE names a file, the first wxpy() call of
+ * the process loads it this way (errors ignored). */
+int wxpy_tune_cache_load(const char *path, int check_device);
+
 /* ---- seeded synthetic inputs ----------------------------------------------------- */
 
 /* Stream tags used by the library's own synthetic inputs (server requests). */

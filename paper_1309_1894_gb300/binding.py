@@ -57,6 +57,22 @@ class VariantInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", VariantInfo), ("best_us", ctypes.c_double),
+                ("default_us", ctypes.c_double), ("reference_us", ctypes.c_double),
+                ("best_gbs", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("rejected", ctypes.c_int32), ("bucket", ctypes.c_int32),
+                ("tune_key", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "best"}
+        d["best"] = self.best.as_dict()
+        return d
+
+
+TUNE_ALIGN16, TUNE_ALIGN8, TUNE_XY, TUNE_WALIAS, TUNE_QUICK, TUNE_RESIDENT = 1, 2, 4, 8, 16, 32
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -79,6 +95,12 @@ SIGNATURES = {
     "wxpy_run_variant": (_INT, [_INT, _I64, _D, _P, _P, _P, _P]),
     "wxpy_reference": (_INT, [_I64, _D, _P, _P, _P, _P]),
     "wxpy_debug_inject_launch_error": (_INT, [_INT, _INT]),
+    "wxpy_tune": (_INT, [_I64, ctypes.c_uint, ctypes.POINTER(TuneResult)]),
+    "wxpy_tune_get": (_INT, [_INT, ctypes.POINTER(_INT)]),
+    "wxpy_tune_set": (_INT, [_INT, _INT]),
+    "wxpy_tune_clear": (_INT, []),
+    "wxpy_tune_cache_save": (_INT, [ctypes.c_char_p]),
+    "wxpy_tune_cache_load": (_INT, [ctypes.c_char_p, _INT]),
     "wxpy_fill_uniform": (_INT, [_I64, ctypes.c_uint64, ctypes.c_uint32, _I64, _D, _D, _P, _P]),
 }
 
@@ -238,3 +260,33 @@ def wxpy_fill_uniform(dst, seed: int, tag: int, lo: float = -1.0, hi: float = 1.
 def wxpy_debug_inject_launch_error(cuda_error: int, count: int) -> None:
     check(lib().wxpy_debug_inject_launch_error(cuda_error, count),
           "wxpy_debug_inject_launch_error")
+
+
+def wxpy_tune(n: int, flags: int = 0) -> dict:
+    """Run the empirical search for the cell of n (and the class in ``flags``)."""
+    r = TuneResult()
+    check(lib().wxpy_tune(n, flags, ctypes.byref(r)), "wxpy_tune")
+    return r.as_dict()
+
+
+def wxpy_tune_get(tune_key: int) -> int:
+    v = _INT()
+    check(lib().wxpy_tune_get(tune_key, ctypes.byref(v)), "wxpy_tune_get")
+    return v.value
+
+
+def wxpy_tune_set(tune_key: int, variant_id: int) -> None:
+    check(lib().wxpy_tune_set(tune_key, variant_id), "wxpy_tune_set")
+
+
+def wxpy_tune_clear() -> None:
+    check(lib().wxpy_tune_clear(), "wxpy_tune_clear")
+
+
+def wxpy_tune_cache_save(path: str) -> None:
+    check(lib().wxpy_tune_cache_save(os.fsencode(path)), "wxpy_tune_cache_save")
+
+
+def wxpy_tune_cache_load(path: str, check_device: bool = True) -> None:
+    check(lib().wxpy_tune_cache_load(os.fsencode(path), int(check_device)),
+          "wxpy_tune_cache_load")

@@ -427,6 +427,7 @@ int wxpy_set_variant(int id) {
 }
 
 static int select_variant(const CallClass &c, int64_t n, Variant *v, int *source) {
+    autoload_tune_cache();
     const int forced = g_forced_variant.load(std::memory_order_relaxed);
     if (forced >= 0 && decode_variant(forced, v)) {
         *source = 2;

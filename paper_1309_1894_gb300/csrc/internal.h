@@ -75,6 +75,9 @@ int run_variant(const Variant &v, const CallClass &c, int64_t n, double alpha,
 // Launch gate for fault injection: returns cudaSuccess or the injected error.
 cudaError_t injected_launch_error();
 
+// tune.cu: loads $WXPY_TUNE_CACHE once per process (errors ignored).
+void autoload_tune_cache();
+
 // gen.cu: seeded device inputs, bitwise comparison, L2 eviction.
 uint64_t stream_key(uint64_t seed, uint32_t tag);
 int launch_fill_uniform(double *dst, int64_t n, uint64_t seed, uint32_t tag, int64_t start,

@@ -1,0 +1,471 @@
+// tune.cu -- the empirical search of paper Sec. 2 applied to the WXPY family,
+// and the persisted table of its results.
+//
+// Sec. 2: the annotated code is turned into variants, each variant is compiled
+// and run to obtain its performance and its outputs, the outputs are compared
+// with the reference results of the unchanged code, and the best-performing
+// variant is the result of the tuning.  Here the variants are the members of
+// the kernel family (Sec. 3 knobs: threads per block, blocks per grid, number
+// of streams, L1 size via the carveout, unroll; plus vector width and cache
+// policy), the reference results come from the plain reference variant run on
+// the same inputs, and a candidate whose output differs by a single bit is
+// rejected.  The winner is stored per (size bucket, alignment class, alias
+// group) cell and used by every later wxpy() call that falls in that cell.
+//
+// Search order (coordinate descent over the knobs, cheapest to tune first):
+//   A. vector width x unroll x cache policy at 256 threads, one-shot grid;
+//   B. threads per block x grid mode, from the best of A;
+//   C. carveout x stream count, from the best of B.
+// Each candidate is timed `reps` times; the median counts.  Before every timed
+// run the L2 is flushed by reading a buffer of twice its size, and a short
+// device delay is queued first so that the host's launch latency is not timed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cerrno>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace wx {
+namespace {
+
+std::mutex g_tune_mu;
+
+__global__ void delay_kernel(long long cycles) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < cycles) __nanosleep(500);
+}
+
+struct Scratch {
+    double *x = nullptr, *y = nullptr, *x0 = nullptr, *wref = nullptr, *wcand = nullptr;
+    void *flush = nullptr;
+    int64_t flush_bytes = 0;
+    unsigned long long *count = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch() {
+        if (s) cudaStreamSynchronize(s);
+        for (void *p : {(void *)x, (void *)y, (void *)x0, (void *)wref, (void *)wcand, flush,
+                        (void *)count})
+            if (p) cudaFree(p);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+// One tuning problem: the call class to reproduce and the pointers that do.
+struct Problem {
+    int64_t n;
+    double alpha;
+    const double *x, *y;
+    double *w;
+    bool w_alias;  // w == x: candidate runs overwrite x
+    CallClass cls;
+};
+
+int alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WXPY_ENOMEM, "tuner scratch allocation of %zu bytes failed", bytes);
+    }
+    return WXPY_OK;
+}
+
+// Median device time (us) of `reps` runs of variant v.
+int time_variant(const Variant &v, const Problem &p, Scratch &sc, int reps, bool flush,
+                 double *median_us) {
+    std::vector<float> ms(reps);
+    for (int r = 0; r < reps; ++r) {
+        int st;
+        if (flush && (st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK)
+            return st;
+        delay_kernel<<<1, 1, 0, sc.s>>>(20000);
+        cudaEventRecord(sc.e0, sc.s);
+        st = run_variant(v, p.cls, p.n, p.alpha, p.x, p.y, p.w, sc.s);
+        if (st != WXPY_OK) return st;
+        cudaEventRecord(sc.e1, sc.s);
+        cudaError_t e = cudaEventSynchronize(sc.e1);
+        if (e != cudaSuccess) return fail_cuda(e, "tuner timing");
+        cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
+    }
+    std::sort(ms.begin(), ms.end());
+    *median_us = 1e3 * (double)ms[reps / 2];
+    return WXPY_OK;
+}
+
+// Runs v once on pristine inputs and counts bit mismatches against wref.
+int verify_variant(const Variant &v, const Problem &p, Scratch &sc, unsigned long long *bad) {
+    const size_t bytes = (size_t)p.n * 8;
+    cudaError_t e = cudaSuccess;
+    double *out = p.w_alias ? (double *)p.x : sc.wcand;
+    if (p.w_alias) e = cudaMemcpyAsync((void *)p.x, sc.x0, bytes, cudaMemcpyDeviceToDevice, sc.s);
+    else e = cudaMemsetAsync(sc.wcand, 0xff, bytes, sc.s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.count, 0, sizeof(unsigned long long), sc.s);
+    if (e != cudaSuccess) return fail_cuda(e, "tuner verify setup");
+    int st = run_variant(v, p.cls, p.n, p.alpha, p.x, p.y, out, sc.s);
+    if (st != WXPY_OK) return st;
+    if ((st = launch_count_mismatch(out, sc.wref, p.n, sc.count, sc.s)) != WXPY_OK) return st;
+    e = cudaMemcpyAsync(bad, sc.count, sizeof *bad, cudaMemcpyDeviceToHost, sc.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sc.s);
+    if (e != cudaSuccess) return fail_cuda(e, "tuner verify");
+    if (p.w_alias) {  // leave x pristine for the timing runs
+        e = cudaMemcpyAsync((void *)p.x, sc.x0, bytes, cudaMemcpyDeviceToDevice, sc.s);
+        if (e != cudaSuccess) return fail_cuda(e, "tuner restore");
+    }
+    return WXPY_OK;
+}
+
+struct Candidate {
+    Variant v;
+    double us;
+};
+
+}  // namespace
+
+int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
+    if (n <= 0) return fail(WXPY_EINVAL, "tune needs n > 0");
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    const bool xy = flags & WXPY_TUNE_XY, walias = flags & WXPY_TUNE_WALIAS;
+    const int off_x = (flags & WXPY_TUNE_ALIGN8) ? 8 : ((flags & WXPY_TUNE_ALIGN16) ? 16 : 0);
+    const bool quick = flags & WXPY_TUNE_QUICK;
+    const bool flush = !(flags & WXPY_TUNE_RESIDENT);
+    if (xy && walias) return fail(WXPY_EINVAL, "choose at most one of XY and WALIAS");
+
+    Scratch sc;
+    const size_t vbytes = (size_t)n * 8 + 64;
+    if ((st = alloc((void **)&sc.x, vbytes)) || (st = alloc((void **)&sc.y, vbytes)) ||
+        (st = alloc((void **)&sc.wref, vbytes)) || (st = alloc((void **)&sc.wcand, vbytes)) ||
+        (st = alloc((void **)&sc.count, 64)))
+        return st;
+    if (walias && (st = alloc((void **)&sc.x0, vbytes))) return st;
+    sc.flush_bytes = std::max<int64_t>(2 * dp->l2_bytes, 64 << 20);
+    if (flush && (st = alloc(&sc.flush, (size_t)sc.flush_bytes))) return st;
+    cudaError_t e = cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&sc.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&sc.e1);
+    if (e != cudaSuccess) return fail_cuda(e, "tuner stream/events");
+    if (flush && (e = cudaMemsetAsync(sc.flush, 0, (size_t)sc.flush_bytes, sc.s)) != cudaSuccess)
+        return fail_cuda(e, "tuner flush init");
+
+    // Inputs: x shifted by off_x bytes relative to y and w reproduces the
+    // requested alignment class; values from the seeded generator.
+    Problem p;
+    p.n = n;
+    p.alpha = 0.5;  // keeps repeated in-place runs bounded
+    double *xs = (double *)((char *)sc.x + off_x);
+    p.x = xs;
+    p.y = xy ? xs : sc.y;
+    p.w = walias ? xs : sc.wcand;
+    p.w_alias = walias;
+    if ((st = launch_fill_uniform(xs, n, 20130907ull, 1, 0, -1.0, 1.0, sc.s)) ||
+        (st = launch_fill_uniform(sc.y, n, 20130907ull, 2, 0, -1.0, 1.0, sc.s)))
+        return st;
+    if (walias && (e = cudaMemcpyAsync(sc.x0, xs, (size_t)n * 8, cudaMemcpyDeviceToDevice, sc.s)) !=
+                      cudaSuccess)
+        return fail_cuda(e, "tuner copy");
+    if ((st = classify(n, p.x, p.y, p.w, &p.cls)) != WXPY_OK) return st;
+
+    // Reference results of Sec. 2: the plain variant on the same inputs.
+    {
+        SingleArgs a{p.x, p.y, sc.wref, p.alpha, n, 0, 0};
+        e = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sc.s);
+        if (e != cudaSuccess) return fail_cuda(e, "tuner reference run");
+    }
+    // Repetitions: more for short runs, whose times are noisier.
+    const double est_us = 24.0 * (double)n / 6.0e3 + 3.0;
+    int reps = est_us > 2000 ? 5 : (est_us > 200 ? 7 : 11);
+    if (quick) reps = std::max(3, reps / 2);
+
+    int candidates = 0, rejected = 0;
+    auto consider = [&](const Variant &raw, std::vector<Candidate> &pool) -> int {
+        const Variant v = adjust_variant(raw, p.cls);
+        for (const auto &c : pool)
+            if (std::memcmp(&c.v, &v, sizeof v) == 0) return WXPY_OK;  // duplicate after adjust
+        unsigned long long bad = 0;
+        int s2 = verify_variant(v, p, sc, &bad);
+        if (s2 != WXPY_OK) return s2;
+        ++candidates;
+        if (bad) {
+            ++rejected;
+            return WXPY_OK;
+        }
+        double us = 0;
+        if ((s2 = time_variant(v, p, sc, reps, flush, &us)) != WXPY_OK) return s2;
+        pool.push_back(Candidate{v, us});
+        return WXPY_OK;
+    };
+    auto best_of = [](const std::vector<Candidate> &pool) {
+        return *std::min_element(pool.begin(), pool.end(),
+                                 [](const Candidate &a, const Candidate &b) { return a.us < b.us; });
+    };
+
+    // Stage A: width x unroll x cache.
+    std::vector<Candidate> A;
+    for (int vb : kVecBytes)
+        for (int u : kUnroll) {
+            if (quick && u == 1) continue;
+            for (int ca : kCache) {
+                if (quick && ca == 0) continue;
+                if ((st = consider(Variant{vb, u, 256, 0, ca, -1, 1}, A)) != WXPY_OK) return st;
+            }
+        }
+    if (A.empty()) return fail(WXPY_EMISMATCH, "every candidate differed from the reference");
+    Candidate best = best_of(A);
+    if (!quick) {
+        // Stage B: block size x grid mode.
+        std::vector<Candidate> B{best};
+        for (int t : kThreads)
+            for (int g : kBlocksPerSm) {
+                Variant v = best.v;
+                v.threads = t;
+                v.blocks_per_sm = g;
+                if ((st = consider(v, B)) != WXPY_OK) return st;
+            }
+        best = best_of(B);
+        // Stage C: carveout x streams (a split needs pieces of >= 65536 elements).
+        std::vector<Candidate> C{best};
+        for (int co : kCarveout)
+            for (int s : kStreams) {
+                if (s > 1 && n / s < 65536) continue;
+                Variant v = best.v;
+                v.carveout = co;
+                v.streams = s;
+                if ((st = consider(v, C)) != WXPY_OK) return st;
+            }
+        best = best_of(C);
+    }
+    // Re-time the winner against the default and the reference variant.
+    double best_us = 0, def_us = 0, ref_us = 0;
+    if ((st = time_variant(best.v, p, sc, reps, flush, &best_us)) != WXPY_OK) return st;
+    const Variant dv = default_variant(p.cls, n);
+    if ((st = time_variant(dv, p, sc, reps, flush, &def_us)) != WXPY_OK) return st;
+    {
+        std::vector<float> ms(reps);
+        for (int r = 0; r < reps; ++r) {
+            if (flush && (st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s))) return st;
+            delay_kernel<<<1, 1, 0, sc.s>>>(20000);
+            cudaEventRecord(sc.e0, sc.s);
+            SingleArgs a{p.x, p.y, p.w, p.alpha, n, 0, 0};
+            e = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
+            if (e != cudaSuccess) return fail_cuda(e, "tuner reference timing");
+            cudaEventRecord(sc.e1, sc.s);
+            if ((e = cudaEventSynchronize(sc.e1)) != cudaSuccess) return fail_cuda(e, "tuner sync");
+            cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
+        }
+        std::sort(ms.begin(), ms.end());
+        ref_us = 1e3 * (double)ms[reps / 2];
+    }
+    // Keep whichever of the winner and the default is faster on the re-timing.
+    Variant chosen = best.v;
+    double chosen_us = best_us;
+    if (def_us < best_us) {
+        chosen = dv;
+        chosen_us = def_us;
+    }
+    const int id = encode_variant(chosen);
+    g_tuned[p.cls.tune_key].store(id);
+    if (out) {
+        std::memset(out, 0, sizeof *out);
+        to_info(chosen, id, &out->best);
+        out->best_us = chosen_us;
+        out->default_us = def_us;
+        out->reference_us = ref_us;
+        const double bytes_per_elem = xy ? 16.0 : 24.0;
+        out->best_gbs = bytes_per_elem * (double)n / (chosen_us * 1e-6) / 1e9;
+        out->candidates = candidates;
+        out->rejected = rejected;
+        out->bucket = p.cls.bucket;
+        out->tune_key = p.cls.tune_key;
+    }
+    return WXPY_OK;
+}
+
+// ---------------------------------------------------------------- tune cache file
+namespace {
+
+std::string device_key(const DeviceProps &d) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|cc%d.%d|sm%d|cudart%d", d.name, d.cc_major, d.cc_minor,
+                  d.sm_count, CUDART_VERSION);
+    return buf;
+}
+
+// Finds the string value of "key": "..." in s (no escapes are written by save).
+bool find_string(const std::string &s, const char *key, std::string *val) {
+    const std::string pat = std::string("\"") + key + "\"";
+    size_t p = s.find(pat);
+    if (p == std::string::npos) return false;
+    p = s.find('"', s.find(':', p + pat.size()) + 1);
+    if (p == std::string::npos) return false;
+    const size_t q = s.find('"', p + 1);
+    if (q == std::string::npos) return false;
+    *val = s.substr(p + 1, q - p - 1);
+    return true;
+}
+
+bool find_int(const std::string &s, size_t from, size_t to, const char *key, long long *val) {
+    const std::string pat = std::string("\"") + key + "\"";
+    size_t p = s.find(pat, from);
+    if (p == std::string::npos || p >= to) return false;
+    p = s.find(':', p + pat.size());
+    if (p == std::string::npos || p >= to) return false;
+    char *end = nullptr;
+    errno = 0;
+    const long long v = std::strtoll(s.c_str() + p + 1, &end, 10);
+    if (errno || end == s.c_str() + p + 1) return false;
+    *val = v;
+    return true;
+}
+
+}  // namespace
+
+int cache_save(const char *path) {
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    std::string out = "{\n  \"format\": \"wxpy-tune-1\",\n  \"device\": \"" + device_key(*dp) +
+                      "\",\n  \"entries\": [";
+    bool first = true;
+    for (int k = 0; k < kTuneKeys; ++k) {
+        const int id = g_tuned[k].load();
+        if (id < 0) continue;
+        Variant v;
+        decode_variant(id, &v);
+        char buf[320];
+        std::snprintf(buf, sizeof buf,
+                      "%s\n    {\"key\": %d, \"bucket\": %d, \"align\": %d, \"group\": %d, "
+                      "\"variant\": %d, \"vec_bytes\": %d, \"unroll\": %d, \"threads\": %d, "
+                      "\"blocks_per_sm\": %d, \"cache\": %d, \"carveout\": %d, \"streams\": %d}",
+                      first ? "" : ",", k, k / 12, (k / 4) % 3 == 0 ? 32 : ((k / 4) % 3 == 1 ? 16 : 8),
+                      k % 4, id, v.vec_bytes, v.unroll, v.threads, v.blocks_per_sm, v.cache,
+                      v.carveout, v.streams);
+        out += buf;
+        first = false;
+    }
+    out += "\n  ]\n}\n";
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(WXPY_EINVAL, "cannot write %s", tmp.c_str());
+    const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
+    std::fclose(f);
+    if (!ok || std::rename(tmp.c_str(), path) != 0)
+        return fail(WXPY_EINVAL, "cannot write %s", path);
+    return WXPY_OK;
+}
+
+int cache_load(const char *path, const char *expect_device) {
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(WXPY_ENOTFOUND, "cannot open %s", path);
+    std::string s;
+    char buf[4096];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, r);
+    std::fclose(f);
+    std::string fmt, dev;
+    if (!find_string(s, "format", &fmt) || fmt != "wxpy-tune-1")
+        return fail(WXPY_EINVAL, "%s: not a wxpy tune cache", path);
+    if (!find_string(s, "device", &dev)) return fail(WXPY_EINVAL, "%s: no device key", path);
+    if (expect_device && dev != expect_device)
+        return fail(WXPY_EINVAL, "%s was tuned on '%s', this device is '%s'", path, dev.c_str(),
+                    expect_device);
+    // Parse every entry first; apply only if all are valid.
+    std::vector<std::pair<int, int>> entries;
+    size_t p = s.find("\"entries\"");
+    if (p == std::string::npos) return fail(WXPY_EINVAL, "%s: no entries", path);
+    while ((p = s.find('{', p + 1)) != std::string::npos) {
+        const size_t q = s.find('}', p);
+        if (q == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated entry", path);
+        long long key = -1, id = -1;
+        if (!find_int(s, p, q, "key", &key) || !find_int(s, p, q, "variant", &id) || key < 0 ||
+            key >= kTuneKeys || id < 0 || id >= kVariantCount)
+            return fail(WXPY_EINVAL, "%s: malformed entry", path);
+        entries.emplace_back((int)key, (int)id);
+        p = q;
+    }
+    for (auto &kv : entries) g_tuned[kv.first].store(kv.second);
+    return WXPY_OK;
+}
+
+std::string current_device_key(int *status) {
+    const DeviceProps *dp = current_device(status);
+    return dp ? device_key(*dp) : std::string();
+}
+
+namespace {
+std::once_flag g_autoload_once;
+}
+
+void autoload_tune_cache() {
+    std::call_once(g_autoload_once, [] {
+        const char *path = std::getenv("WXPY_TUNE_CACHE");
+        if (!path || !*path) return;
+        int st = WXPY_OK;
+        const std::string key = current_device_key(&st);
+        if (st == WXPY_OK) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            cache_load(path, key.c_str());
+        }
+        clear_error();
+    });
+}
+
+}  // namespace wx
+
+using namespace wx;
+
+extern "C" {
+
+int wxpy_tune(int64_t n, unsigned flags, wxpy_tune_result *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return tune_impl(n, flags, out);
+}
+
+int wxpy_tune_get(int tune_key, int *variant_id) {
+    if (tune_key < 0 || tune_key >= kTuneKeys || !variant_id)
+        return fail(WXPY_EINVAL, "bad tune key %d", tune_key);
+    *variant_id = g_tuned[tune_key].load();
+    return WXPY_OK;
+}
+
+int wxpy_tune_set(int tune_key, int variant_id) {
+    if (tune_key < 0 || tune_key >= kTuneKeys) return fail(WXPY_EINVAL, "bad tune key %d", tune_key);
+    if (variant_id < -1 || variant_id >= kVariantCount)
+        return fail(WXPY_EINVAL, "bad variant id %d", variant_id);
+    g_tuned[tune_key].store(variant_id);
+    return WXPY_OK;
+}
+
+int wxpy_tune_clear(void) {
+    for (auto &t : g_tuned) t.store(-1);
+    return WXPY_OK;
+}
+
+int wxpy_tune_cache_save(const char *path) {
+    if (!path) return fail(WXPY_EINVAL, "null path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return cache_save(path);
+}
+
+int wxpy_tune_cache_load(const char *path, int check_device) {
+    if (!path) return fail(WXPY_EINVAL, "null path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!check_device) return cache_load(path, nullptr);
+    int st = WXPY_OK;
+    const std::string key = current_device_key(&st);
+    if (st != WXPY_OK) return st;
+    return cache_load(path, key.c_str());
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""GPU tests of the empirical search (paper Sec. 2) through the C ABI.
+
+The search must reject no variant (every family member reproduces the
+reference results bit for bit), store its winner in the cell of the call's
+size bucket and class, and the tuned path must still match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import synth
+from gpu_util import Guarded, bits_equal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _clean_table():
+    wx.wxpy_set_variant(-1)
+    wx.wxpy_tune_clear()
+    yield
+    wx.wxpy_tune_clear()
+
+
+def _case(n, offs=(0, 0, 0)):
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + n, n)
+    gx, gy, gw = Guarded(n, offs[0]).set(xh), Guarded(n, offs[1]).set(yh), Guarded(n, offs[2])
+    return alpha, xh, yh, gx, gy, gw
+
+
+@pytest.mark.parametrize("n", [(1 << 12) + 3, (1 << 18), (1 << 22) + 3])
+def test_full_search_selects_and_is_used(n):
+    r = wx.wxpy_tune(n)
+    assert r["rejected"] == 0 and r["candidates"] >= 20
+    assert r["bucket"] == n.bit_length() - 1
+    assert r["best_us"] > 0 and r["best_us"] <= r["default_us"] * 1.0001
+    assert wx.wxpy_tune_get(r["tune_key"]) == r["best"]["id"]
+    alpha, xh, yh, gx, gy, gw = _case(n)
+    v, src = wx.wxpy_lookup(gx.t, gy.t, gw.t)
+    assert src == 1 and v["id"] == r["best"]["id"]
+    wx.wxpy(alpha, gx.t, gy.t, gw.t)
+    torch.cuda.synchronize()
+    ok, msg = bits_equal(gw.t, oracle.wxpy(alpha, xh, yh))
+    assert ok, msg
+    for g in (gx, gy, gw):
+        g.check()
+
+
+@pytest.mark.parametrize("flags,offs,alias", [
+    (wx.TUNE_ALIGN16 | wx.TUNE_QUICK, (16, 0, 0), None),
+    (wx.TUNE_ALIGN8 | wx.TUNE_QUICK, (8, 0, 0), None),
+    (wx.TUNE_XY | wx.TUNE_QUICK, (0, 0, 0), "xy"),
+    (wx.TUNE_WALIAS | wx.TUNE_QUICK, (0, 0, 0), "wx"),
+    (wx.TUNE_RESIDENT | wx.TUNE_QUICK, (0, 0, 0), None),
+])
+def test_class_search(flags, offs, alias):
+    n = 100003
+    r = wx.wxpy_tune(n, flags)
+    assert r["rejected"] == 0 and r["candidates"] > 0
+    alpha, xh, yh, gx, gy, gw = _case(n, offs)
+    x, y, w = gx.t, gy.t, gw.t
+    if alias == "xy":
+        y, yh = x, xh
+    if alias == "wx":
+        w = x
+    c = wx.wxpy_classify(n, x.data_ptr(), y.data_ptr(), w.data_ptr())
+    assert c["tune_key"] == r["tune_key"]
+    v, src = wx.wxpy_lookup(x, y, w)
+    assert src == 1
+    wx.wxpy(alpha, x, y, w)
+    torch.cuda.synchronize()
+    ok, msg = bits_equal(w, oracle.wxpy(alpha, xh, yh))
+    assert ok, msg
+
+
+def test_cache_roundtrip(tmp_path):
+    r1 = wx.wxpy_tune((1 << 14) + 3, wx.TUNE_QUICK)
+    r2 = wx.wxpy_tune(1 << 20, wx.TUNE_QUICK)
+    path = str(tmp_path / "tune.json")
+    wx.wxpy_tune_cache_save(path)
+    wx.wxpy_tune_clear()
+    assert wx.wxpy_tune_get(r1["tune_key"]) == -1
+    wx.wxpy_tune_cache_load(path, check_device=True)
+    assert wx.wxpy_tune_get(r1["tune_key"]) == r1["best"]["id"]
+    assert wx.wxpy_tune_get(r2["tune_key"]) == r2["best"]["id"]
+    # a file from another device is refused and changes nothing
+    text = open(path).read().replace("GB300", "OtherGPU").replace("NVIDIA", "Other")
+    other = tmp_path / "other.json"
+    other.write_text(text)
+    wx.wxpy_tune_clear()
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy_tune_cache_load(str(other), check_device=True)
+    assert e.value.status == wx.WXPY_EINVAL
+    assert wx.wxpy_tune_get(r1["tune_key"]) == -1
+
+
+def test_tuned_sweep_parity():
+    """Tune a few buckets, then the sweep sizes of those buckets match the oracle."""
+    for k in (10, 15, 20):
+        wx.wxpy_tune(1 << k, wx.TUNE_QUICK)
+    for k in (10, 15, 20):
+        for n in (1 << k, (1 << k) + 3):
+            for off in (0, 8, 24):
+                alpha, xh, yh, gx, gy, gw = _case(n, (off, off, off))
+                wx.wxpy(alpha, gx.t, gy.t, gw.t)
+                torch.cuda.synchronize()
+                ok, msg = bits_equal(gw.t, oracle.wxpy(alpha, xh, yh))
+                assert ok, f"n={n} off={off}: {msg}"
+                for g in (gx, gy, gw):
+                    g.check()
