@@ -400,6 +400,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_extras:
         result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
+        result["batched"] = measure_batched(wx, lib, torch, dev, sh, stream, peak)
     if rank == 0:
         rate1, passes, dt = cpu_oracle_rate(24, args.cpu_seconds, threads=1)
         cores = host_cores()
@@ -527,6 +528,83 @@ def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
             "d2h_bytes_per_step": d2h, "steps": steps,
             "how": "per call: pinned host x, y -> device, wxpy(), device w -> pinned host, "
                    "one stream, copies inside the timed region"}
+
+
+def batch_layout(ns):
+    """Segment starts (elements) at 256-byte boundaries, and the arena length."""
+    starts, pos = [], 0
+    for n in ns:
+        starts.append(pos)
+        pos += (int(n) + 31) // 32 * 32
+    return starts, pos
+
+
+def measure_batched(wx, lib, torch, dev, sh, stream, peak, reps=20, per_call_reps=3):
+    """4096 independent problems, n log-uniform in [1, 2^20] (about 3.1e8
+    elements, 7.4 GB per batch), alpha_i ~ U(-2,2), values U(-1,1): one
+    persistent segmented launch replayed from a CUDA graph, versus the same
+    launch without the graph, versus 4096 wxpy() calls on one stream."""
+    from paper_1309_1894_gb300 import synth
+    seed = synth.BASE_SEED + 3
+    ns = synth.log_uniform_lengths(seed, 4096, 1, 1 << 20)
+    starts, total = batch_layout(ns)
+    x = torch.empty(total, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    w = torch.empty_like(x)
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    alphas = synth.uniform_pm2(seed, synth.TAG_ALPHA, len(ns))
+    px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
+    table = wx.desc_table(ns, alphas, [px + 8 * s for s in starts], [py + 8 * s for s in starts],
+                          [pw + 8 * s for s in starts])
+    dt = wx.table_to_device(table)
+    t0 = time.perf_counter()
+    tune = wx.wxpy_batch_tune(0, 20, 0)
+    tune_s = time.perf_counter() - t0
+    plan = wx.wxpy_batch_plan_create(table)
+    info = plan.info()
+    elems = int(sum(int(n) for n in ns))
+    nbytes = BYTES_PER_ELEM * elems
+
+    def timed(fn, r):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(r):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / r
+
+    ms_graph = timed(lambda: plan.graph_launch(dt, stream=sh), reps)
+    ms_launch = timed(lambda: plan.launch(dt, stream=sh), reps)
+    calls = [(int(n), float(a), px + 8 * s, py + 8 * s, pw + 8 * s)
+             for n, a, s in zip(ns, alphas, starts)]
+
+    def per_call():
+        for (n, a, xa, ya, wa) in calls:
+            lib.wxpy(n, a, xa, ya, wa, sh)
+
+    ms_calls = timed(per_call, per_call_reps)
+    plan.close()
+    del x, y, w, dt
+    torch.cuda.empty_cache()
+
+    def row(ms):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        return {"ms": ms, "gbs": gbs, "elem_per_s": elems / (ms / 1e3), "frac_of_peak": gbs / peak}
+
+    return {"segments": len(ns), "elements": elems, "bytes": nbytes, "tiles": info["tiles"],
+            "grid": info["grid"], "graph_replay": row(ms_graph), "persistent_launch": row(ms_launch),
+            "per_call_launches": row(ms_calls), "speedup_graph_vs_per_call": ms_calls / ms_graph,
+            "search": {"seconds": tune_s, "candidates": tune["candidates"],
+                       "rejected": tune["rejected"], "blocks_per_sm": tune["blocks_per_sm"],
+                       "mixed_gbs": tune["mixed_gbs"],
+                       "shapes": {r["bucket"]: [r["tile_elems"], r["unroll"]]
+                                  for r in tune["buckets"]}}}
 
 
 def measure_streams(wx, lib, torch, dev, sh, stream, peak, reps=50, warm=10):

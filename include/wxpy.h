@@ -174,6 +174,69 @@ int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,
 int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
                    double *w, void *stream);
 
+/* ---- batched launch: many independent problems in one launch ----------------- */
+
+/* One problem of a batch: w = RN(RN(alpha*x) + y) over n elements (Sec. 3,
+ * Fig. 1 vecwxpy).  40 bytes, no padding.  Pointers are device addresses. */
+typedef struct wxpy_desc {
+    int64_t n;
+    double alpha;
+    const double *x;
+    const double *y;
+    double *w;
+} wxpy_desc;
+
+typedef struct wxpy_batch_plan wxpy_batch_plan; /* opaque */
+
+typedef struct wxpy_batch_info {
+    int64_t segments;  /* descriptors in the table */
+    int64_t tiles;     /* work items of the persistent launch */
+    int64_t elements;  /* sum of n */
+    int64_t bytes;     /* algorithmic bytes: 24 per element */
+    int32_t grid;      /* blocks of the launch */
+    int32_t threads;   /* threads per block */
+} wxpy_batch_info;
+
+/* Builds a plan for the problems in `host_table` (a HOST copy of the table;
+ * only its lengths and pointer values are read, never the vectors).  Every
+ * descriptor is validated as wxpy() validates a call, and the problems must be
+ * independent: no two write overlapping ranges and none reads a range another
+ * writes (WXPY_EOVERLAP).  Validation happens before any CUDA call.  The plan
+ * cuts each problem into tiles whose length depends on its size bucket (tuned
+ * by wxpy_batch_tune, else built in) and uploads the tile list to device
+ * memory that the plan owns.  Synchronous.  *out is NULL on error. */
+int wxpy_batch_plan_create(const wxpy_desc *host_table, int64_t count,
+                           wxpy_batch_plan **out);
+
+/* Runs every problem of the plan in ONE persistent kernel launch on `stream`
+ * (asynchronous).  `dev_table` is a DEVICE copy of the table, owned by the
+ * caller, with the same lengths as the host table of the plan; alpha and the
+ * pointers are read from it at run time.  A tile that would pass the n of the
+ * descriptor it reads is skipped and flagged (wxpy_batch_status).  May be
+ * captured in a CUDA graph.  A plan serves one host thread at a time. */
+int wxpy_batch_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *stream);
+
+/* The same launch replayed from a CUDA graph that the plan builds on first use
+ * (and re-points, by updating the kernel node, when dev_table changes). */
+int wxpy_batch_graph_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table,
+                            void *stream);
+
+int wxpy_batch_plan_info(const wxpy_batch_plan *plan, wxpy_batch_info *out);
+
+/* Reads (synchronously) the plan's status word: bit 0 set if a launch skipped
+ * a tile because the device table's n was smaller than the plan's.  clear != 0
+ * resets it. */
+int wxpy_batch_status(wxpy_batch_plan *plan, unsigned *status, int clear);
+
+/* Frees the plan and its device memory (the caller must make sure no launch
+ * of it is still running).  NULL is a no-op. */
+int wxpy_batch_plan_destroy(wxpy_batch_plan *plan);
+
+/* One-shot form: validate, plan and launch in one call.  The tile list lives
+ * in stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on `stream`). */
+int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t count,
+               void *stream);
+
 /* ---- the empirical search (Sec. 2) and its persisted results ------------------ */
 
 /* Which call class wxpy_tune() reproduces (default: x, y, w 32-byte co-aligned
@@ -233,6 +296,38 @@ int wxpy_tune_cache_save(const char *path);
  * environment variable WXPY_TUNE_CACHE names a file, the first wxpy() call of
  * the process loads it this way (errors ignored). */
 int wxpy_tune_cache_load(const char *path, int check_device);
+
+/* ---- the search for the batched launch (Sec. 2 applied per size bucket) ------- */
+
+typedef struct wxpy_batch_tune_result {
+    int32_t tile_elems[64];  /* per bucket: elements per tile, 0 = whole segment */
+    int32_t unroll[64];      /* per bucket: 1, 2, 4, 8 (0 where not searched) */
+    double us[64];           /* per bucket: median time of the bucket's batch */
+    double gbs[64];          /* per bucket: algorithmic GB/s of that batch */
+    double mixed_us;         /* mixed batch of buckets min..max, chosen grid */
+    double mixed_gbs;
+    int32_t blocks_per_sm;   /* chosen grid: blocks_per_sm * sm_count */
+    int32_t threads;
+    int32_t candidates;      /* batched launches run */
+    int32_t rejected;        /* candidates whose output differed from the reference */
+} wxpy_batch_tune_result;
+
+/* For each size bucket b in [bucket_min, bucket_max] (at most 30): builds a
+ * synthetic batch whose segments all fall in b, obtains its reference results
+ * by running the plain reference variant on every segment, then runs the
+ * batched launch with every (tile length, unroll) candidate, rejects any
+ * whose output differs by a bit, and keeps the fastest (median time) for b.
+ * Finally picks blocks per SM on a mixed batch.  The results replace the
+ * process's batch shape table, used by later plans.  Synchronous; allocates
+ * and frees its own scratch.  flags: WXPY_TUNE_QUICK narrows the search. */
+int wxpy_batch_tune(int bucket_min, int bucket_max, unsigned flags,
+                    wxpy_batch_tune_result *out);
+
+/* The batch shape table: per bucket tile length (0 or a multiple of 32, at
+ * most 2^30) and unroll (1, 2, 4, 8).  Host only; no device touched. */
+int wxpy_batch_shape_get(int bucket, int *tile_elems, int *unroll);
+int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll);
+int wxpy_batch_shape_reset(void);
 
 /* ---- seeded synthetic inputs ----------------------------------------------------- */
 

@@ -102,6 +102,17 @@ SIGNATURES = {
     "wxpy_tune_cache_save": (_INT, [ctypes.c_char_p]),
     "wxpy_tune_cache_load": (_INT, [ctypes.c_char_p, _INT]),
     "wxpy_fill_uniform": (_INT, [_I64, ctypes.c_uint64, ctypes.c_uint32, _I64, _D, _D, _P, _P]),
+    "wxpy_batch_plan_create": (_INT, [_P, _I64, ctypes.POINTER(_P)]),
+    "wxpy_batch_launch": (_INT, [_P, _P, _P]),
+    "wxpy_batch_graph_launch": (_INT, [_P, _P, _P]),
+    "wxpy_batch_plan_info": (_INT, [_P, _P]),
+    "wxpy_batch_status": (_INT, [_P, ctypes.POINTER(ctypes.c_uint), _INT]),
+    "wxpy_batch_plan_destroy": (_INT, [_P]),
+    "wxpy_batch": (_INT, [_P, _P, _I64, _P]),
+    "wxpy_batch_tune": (_INT, [_INT, _INT, ctypes.c_uint, _P]),
+    "wxpy_batch_shape_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
+    "wxpy_batch_shape_reset": (_INT, []),
 }
 
 _lock = threading.Lock()
@@ -290,3 +301,117 @@ def wxpy_tune_cache_save(path: str) -> None:
 def wxpy_tune_cache_load(path: str, check_device: bool = True) -> None:
     check(lib().wxpy_tune_cache_load(os.fsencode(path), int(check_device)),
           "wxpy_tune_cache_load")
+
+
+# ---------------------------------------------------------------- batched launch
+# numpy layout of wxpy_desc (40 bytes): n, alpha, x, y, w
+DESC_DTYPE = [("n", "<i8"), ("alpha", "<f8"), ("x", "<u8"), ("y", "<u8"), ("w", "<u8")]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("elements", ctypes.c_int64), ("bytes", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("tile_elems", ctypes.c_int32 * 64), ("unroll", ctypes.c_int32 * 64),
+                ("us", ctypes.c_double * 64), ("gbs", ctypes.c_double * 64),
+                ("mixed_us", ctypes.c_double), ("mixed_gbs", ctypes.c_double),
+                ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32)]
+
+
+def desc_table(ns, alphas, xptrs, yptrs, wptrs):
+    """Host descriptor table (numpy structured array with the wxpy_desc layout)."""
+    import numpy as np
+    t = np.zeros(len(ns), dtype=DESC_DTYPE)
+    t["n"], t["alpha"], t["x"], t["y"], t["w"] = ns, alphas, xptrs, yptrs, wptrs
+    assert t.itemsize == 40
+    return t
+
+
+def table_to_device(table, device="cuda"):
+    """A device copy of a host descriptor table (torch uint8 tensor)."""
+    import numpy as np
+    import torch
+    raw = np.ascontiguousarray(table).view(np.uint8)
+    return torch.from_numpy(raw.copy()).to(device)
+
+
+def _tptr(table) -> int:
+    return table.ctypes.data if len(table) else 0
+
+
+class BatchPlan:
+    """Owns a wxpy_batch_plan (freed on close/del)."""
+
+    def __init__(self, host_table):
+        self.table = host_table
+        h = _P()
+        check(lib().wxpy_batch_plan_create(_tptr(host_table), len(host_table), ctypes.byref(h)),
+              "wxpy_batch_plan_create")
+        self.handle = h.value
+
+    def launch(self, dev_table, stream=None):
+        check(lib().wxpy_batch_launch(self.handle, dev_table.data_ptr(), _stream_handle(stream)),
+              "wxpy_batch_launch")
+
+    def graph_launch(self, dev_table, stream=None):
+        check(lib().wxpy_batch_graph_launch(self.handle, dev_table.data_ptr(),
+                                            _stream_handle(stream)), "wxpy_batch_graph_launch")
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        check(lib().wxpy_batch_plan_info(self.handle, ctypes.byref(i)), "wxpy_batch_plan_info")
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def status(self, clear: bool = False) -> int:
+        s = ctypes.c_uint()
+        check(lib().wxpy_batch_status(self.handle, ctypes.byref(s), int(clear)), "wxpy_batch_status")
+        return s.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wxpy_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wxpy_batch_plan_create(host_table) -> BatchPlan:
+    return BatchPlan(host_table)
+
+
+def wxpy_batch(host_table, dev_table, stream=None) -> None:
+    check(lib().wxpy_batch(_tptr(host_table), dev_table.data_ptr() if len(host_table) else 0,
+                           len(host_table), _stream_handle(stream)), "wxpy_batch")
+
+
+def wxpy_batch_tune(bucket_min: int, bucket_max: int, flags: int = 0) -> dict:
+    r = BatchTuneResult()
+    check(lib().wxpy_batch_tune(bucket_min, bucket_max, flags, ctypes.byref(r)), "wxpy_batch_tune")
+    per = [{"bucket": b, "tile_elems": r.tile_elems[b], "unroll": r.unroll[b], "us": r.us[b],
+            "gbs": r.gbs[b]} for b in range(bucket_min, bucket_max + 1)]
+    return {"buckets": per, "mixed_us": r.mixed_us, "mixed_gbs": r.mixed_gbs,
+            "blocks_per_sm": r.blocks_per_sm, "threads": r.threads,
+            "candidates": r.candidates, "rejected": r.rejected}
+
+
+def wxpy_batch_shape_get(bucket: int) -> tuple[int, int]:
+    t, u = _INT(), _INT()
+    check(lib().wxpy_batch_shape_get(bucket, ctypes.byref(t), ctypes.byref(u)),
+          "wxpy_batch_shape_get")
+    return t.value, u.value
+
+
+def wxpy_batch_shape_set(bucket: int, tile_elems: int, unroll: int) -> None:
+    check(lib().wxpy_batch_shape_set(bucket, tile_elems, unroll), "wxpy_batch_shape_set")
+
+
+def wxpy_batch_shape_reset() -> None:
+    check(lib().wxpy_batch_shape_reset(), "wxpy_batch_shape_reset")

@@ -75,6 +75,18 @@ int run_variant(const Variant &v, const CallClass &c, int64_t n, double alpha,
 // Launch gate for fault injection: returns cudaSuccess or the injected error.
 cudaError_t injected_launch_error();
 
+// ---- batched launch (batch.cu) ----
+struct BatchShape {
+    int threads;                   // block size of the persistent kernel
+    int blocks_per_sm;             // grid = blocks_per_sm * sm_count (capped by tiles)
+    int32_t tile_elems[kBuckets];  // per size bucket of a segment; 0 = whole segment
+    int8_t unroll_log2[kBuckets];  // per size bucket: log2 of the unroll
+};
+BatchShape default_batch_shape();
+BatchShape current_batch_shape();
+void set_batch_shape(const BatchShape &s);
+int validate_table(const wxpy_desc *t, int64_t count);
+
 // tune.cu: loads $WXPY_TUNE_CACHE once per process (errors ignored).
 void autoload_tune_cache();
 

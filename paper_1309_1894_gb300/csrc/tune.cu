@@ -335,8 +335,22 @@ int cache_save(const char *path) {
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);
     if (!dp) return st;
-    std::string out = "{\n  \"format\": \"wxpy-tune-1\",\n  \"device\": \"" + device_key(*dp) +
-                      "\",\n  \"entries\": [";
+    std::string out = "{\n  \"format\": \"wxpy-tune-1\",\n  \"device\": \"" + device_key(*dp) + "\",";
+    {
+        const BatchShape bs = current_batch_shape();
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "\n  \"batch_launch\": {\"threads\": %d, \"blocks_per_sm\": %d},",
+                      bs.threads, bs.blocks_per_sm);
+        out += buf;
+        out += "\n  \"batch\": [";
+        for (int b = 0; b < kBuckets; ++b) {
+            std::snprintf(buf, sizeof buf, "%s\n    {\"bucket\": %d, \"tile\": %d, \"unroll_log2\": %d}",
+                          b ? "," : "", b, bs.tile_elems[b], (int)bs.unroll_log2[b]);
+            out += buf;
+        }
+        out += "\n  ],";
+    }
+    out += "\n  \"entries\": [";
     bool first = true;
     for (int k = 0; k < kTuneKeys; ++k) {
         const int id = g_tuned[k].load();
@@ -384,7 +398,9 @@ int cache_load(const char *path, const char *expect_device) {
     std::vector<std::pair<int, int>> entries;
     size_t p = s.find("\"entries\"");
     if (p == std::string::npos) return fail(WXPY_EINVAL, "%s: no entries", path);
-    while ((p = s.find('{', p + 1)) != std::string::npos) {
+    const size_t entries_end = s.find(']', p);
+    if (entries_end == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated entries", path);
+    while ((p = s.find('{', p + 1)) != std::string::npos && p < entries_end) {
         const size_t q = s.find('}', p);
         if (q == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated entry", path);
         long long key = -1, id = -1;
@@ -394,7 +410,39 @@ int cache_load(const char *path, const char *expect_device) {
         entries.emplace_back((int)key, (int)id);
         p = q;
     }
+    // Optional batch shapes (written by this library since the batched launch).
+    BatchShape bs = current_batch_shape();
+    bool have_batch = false;
+    size_t bpos = s.find("\"batch\"");
+    if (bpos != std::string::npos) {
+        const size_t bend = s.find(']', bpos);
+        if (bend == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated batch", path);
+        size_t q = bpos;
+        while ((q = s.find('{', q + 1)) != std::string::npos && q < bend) {
+            const size_t r = s.find('}', q);
+            long long b = -1, tile = -1, ul = -1;
+            if (r == std::string::npos || !find_int(s, q, r, "bucket", &b) ||
+                !find_int(s, q, r, "tile", &tile) || !find_int(s, q, r, "unroll_log2", &ul) ||
+                b < 0 || b >= kBuckets || tile < 0 || tile > (1 << 30) || (tile % 32) || ul < 0 || ul > 3)
+                return fail(WXPY_EINVAL, "%s: malformed batch entry", path);
+            bs.tile_elems[b] = (int32_t)tile;
+            bs.unroll_log2[b] = (int8_t)ul;
+            q = r;
+        }
+        have_batch = true;
+        const size_t lpos = s.find("\"batch_launch\"");
+        if (lpos != std::string::npos) {
+            const size_t lend = s.find('}', lpos);
+            long long th = -1, bps = -1;
+            if (lend == std::string::npos || !find_int(s, lpos, lend, "threads", &th) ||
+                !find_int(s, lpos, lend, "blocks_per_sm", &bps) || th != 256 || bps < 1 || bps > 32)
+                return fail(WXPY_EINVAL, "%s: malformed batch_launch", path);
+            bs.threads = (int)th;
+            bs.blocks_per_sm = (int)bps;
+        }
+    }
     for (auto &kv : entries) g_tuned[kv.first].store(kv.second);
+    if (have_batch) set_batch_shape(bs);
     return WXPY_OK;
 }
 
