@@ -237,6 +237,7 @@ int wxpy_batch_plan_destroy(wxpy_batch_plan *plan);
 int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t count,
                void *stream);
 
+
 /* ---- the empirical search (Sec. 2) and its persisted results ------------------ */
 
 /* Which call class wxpy_tune() reproduces (default: x, y, w 32-byte co-aligned
@@ -301,7 +302,7 @@ int wxpy_tune_cache_load(const char *path, int check_device);
 
 typedef struct wxpy_batch_tune_result {
     int32_t tile_elems[64];  /* per bucket: elements per tile, 0 = whole segment */
-    int32_t unroll[64];      /* per bucket: 1, 2, 4, 8 (0 where not searched) */
+    int32_t unroll[64];      /* per bucket: 1, 2, 4 (0 where not searched) */
     double us[64];           /* per bucket: median time of the bucket's batch */
     double gbs[64];          /* per bucket: algorithmic GB/s of that batch */
     double mixed_us;         /* mixed batch of buckets min..max, chosen grid */
@@ -324,7 +325,8 @@ int wxpy_batch_tune(int bucket_min, int bucket_max, unsigned flags,
                     wxpy_batch_tune_result *out);
 
 /* The batch shape table: per bucket tile length (0 or a multiple of 32, at
- * most 2^30) and unroll (1, 2, 4, 8).  Host only; no device touched. */
+ * most 2^30) and unroll (1, 2, 4: 32-byte vectors of x and of y in flight per
+ * lane per pass).  Host only; no device touched. */
 int wxpy_batch_shape_get(int bucket, int *tile_elems, int *unroll);
 int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll);
 int wxpy_batch_shape_reset(void);

@@ -26,10 +26,12 @@
 namespace wx {
 
 struct TileRec {
-    int64_t begin;  // first element of the tile within its segment
-    int32_t seg;    // segment index in the descriptor table
-    int32_t len;    // elements in the tile
+    int64_t begin;     // first element of the tile within its segment
+    int32_t seg;       // segment index in the descriptor table
+    uint32_t len_ul;   // bits 0..29: elements in the tile; bits 30..31: log2 unroll
 };
+constexpr uint32_t kLenMask = (1u << 30) - 1;
+constexpr int64_t kMaxTileElems = (1 << 30) - 32;
 static_assert(sizeof(TileRec) == 16, "tile records are 16 bytes");
 static_assert(sizeof(wxpy_desc) == 40, "descriptor layout");
 
@@ -37,57 +39,39 @@ struct SegParams {
     const wxpy_desc *table;
     const TileRec *tiles;
     int64_t ntiles;
-    unsigned *status;             // bit 0: a tile exceeded its descriptor's n
-    int8_t unroll_log2[kBuckets]; // per size bucket of the segment
+    unsigned *status;  // bit 0: a tile exceeded its descriptor's n
 };
 
 namespace {
 
-template <int VW, int U>
-__device__ __forceinline__ void seg_body(const double *x, const double *y, double *w, double alpha,
-                                         int64_t nch, int lane) {
-    for (int64_t c0 = lane; c0 < nch; c0 += 32 * U) {
-        double xv[U][VW], yv[U][VW], wv[U][VW];
-        if (c0 + 32 * (U - 1) < nch) {
+// One pass: up to kMaxU 32-byte vectors of x and y per lane -- the tile's
+// unroll U decides how many -- all loads issued before any store.  The unroll
+// is a run-time predicate on one fixed-size body, so a single body serves
+// every bucket; a body per (width, unroll) behind a switch made the compiler
+// spill.
+constexpr int kMaxU = 4;
+
+__device__ __forceinline__ void seg_body4(const double *x, const double *y, double *w,
+                                          double alpha, int64_t nch, int lane, int U) {
+    const int64_t step = 32 * U;
+    for (int64_t c0 = lane; c0 < nch; c0 += step) {
+        double xv[kMaxU][4], yv[kMaxU][4], wv[kMaxU][4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                ld_vec<VW, 2>(x + (c0 + 32 * u) * VW, xv[u]);
-                ld_vec<VW, 2>(y + (c0 + 32 * u) * VW, yv[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                wxpy_vec<VW>(alpha, xv[u], yv[u], wv[u]);
-                st_vec<VW, 2>(w + (c0 + 32 * u) * VW, wv[u]);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t c = c0 + 32 * u;
-                if (c < nch) {
-                    ld_vec<VW, 2>(x + c * VW, xv[u]);
-                    ld_vec<VW, 2>(y + c * VW, yv[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t c = c0 + 32 * u;
-                if (c < nch) {
-                    wxpy_vec<VW>(alpha, xv[u], yv[u], wv[u]);
-                    st_vec<VW, 2>(w + c * VW, wv[u]);
-                }
+        for (int u = 0; u < kMaxU; ++u) {
+            const int64_t c = c0 + 32 * u;
+            if (u < U && c < nch) {
+                ld_vec<4, 2>(x + c * 4, xv[u]);
+                ld_vec<4, 2>(y + c * 4, yv[u]);
             }
         }
-    }
-}
-
-template <int VW>
-__device__ __forceinline__ void seg_body_u(int ulog, const double *x, const double *y, double *w,
-                                           double alpha, int64_t nch, int lane) {
-    switch (ulog) {
-        case 0: seg_body<VW, 1>(x, y, w, alpha, nch, lane); break;
-        case 1: seg_body<VW, 2>(x, y, w, alpha, nch, lane); break;
-        case 2: seg_body<VW, 4>(x, y, w, alpha, nch, lane); break;
-        default: seg_body<VW, 8>(x, y, w, alpha, nch, lane); break;
+#pragma unroll
+        for (int u = 0; u < kMaxU; ++u) {
+            const int64_t c = c0 + 32 * u;
+            if (u < U && c < nch) {
+                wxpy_vec<4>(alpha, xv[u], yv[u], wv[u]);
+                st_vec<4, 2>(w + c * 4, wv[u]);
+            }
+        }
     }
 }
 
@@ -102,34 +86,37 @@ __device__ __forceinline__ void scalar_op(const double *x, const double *y, doub
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) wxpy_seg_kernel(const SegParams p) {
+__global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = warp; t < p.ntiles; t += nwarps) {
         const TileRec r = p.tiles[t];
         const wxpy_desc d = p.table[r.seg];
-        if (r.begin < 0 || r.len <= 0 || r.begin + r.len > d.n) {
+        const int64_t len = (int64_t)(r.len_ul & kLenMask);
+        if (r.begin < 0 || len <= 0 || r.begin + len > d.n) {
             if (lane == 0) atomicOr(p.status, 1u);
             continue;
         }
         const double *x = d.x + r.begin;
         const double *y = d.y + r.begin;
         double *w = d.w + r.begin;
-        const int64_t len = r.len;
         const uintptr_t ax = (uintptr_t)x, ay = (uintptr_t)y, aw = (uintptr_t)w;
-        const int vw = (((ax ^ aw) | (ay ^ aw)) & 31u) == 0 ? 4
-                     : ((((ax ^ aw) | (ay ^ aw)) & 15u) == 0 ? 2 : 1);
-        const int64_t head = min(len, (int64_t)((vw - (int)((aw >> 3) & (vw - 1))) & (vw - 1)));
-        const int64_t nch = (len - head) / vw;
-        const int64_t body_end = head + nch * vw;
-        const int ulog = p.unroll_log2[63 - __clzll((unsigned long long)d.n)];
-        // Head and tail (each < vw elements) by the first lanes.
-        if (lane < head) scalar_op(x, y, w, d.alpha, lane);
-        if (lane >= 4 && body_end + (lane - 4) < len) scalar_op(x, y, w, d.alpha, body_end + (lane - 4));
-        if (vw == 4) seg_body_u<4>(ulog, x + head, y + head, w + head, d.alpha, nch, lane);
-        else if (vw == 2) seg_body_u<2>(ulog, x + head, y + head, w + head, d.alpha, nch, lane);
-        else seg_body_u<1>(ulog, x + head, y + head, w + head, d.alpha, nch, lane);
+        if ((((ax ^ aw) | (ay ^ aw)) & 31u) == 0) {
+            // x, y, w share their offset mod 32 bytes: peel to the boundary,
+            // stream 32-byte vectors, finish the tail.
+            const int64_t head = min(len, (int64_t)((4 - (int)((aw >> 3) & 3)) & 3));
+            const int64_t nch = (len - head) / 4;
+            const int64_t body_end = head + nch * 4;
+            if (lane < head) scalar_op(x, y, w, d.alpha, lane);
+            if (lane >= 4 && body_end + (lane - 4) < len)
+                scalar_op(x, y, w, d.alpha, body_end + (lane - 4));
+            seg_body4(x + head, y + head, w + head, d.alpha, nch, lane, 1 << (r.len_ul >> 30));
+        } else {
+            // Pointers that share less than 32-byte alignment (rare: separate
+            // allocations are 256-byte aligned): coalesced 8-byte accesses.
+            for (int64_t e = lane; e < len; e += 32) scalar_op(x, y, w, d.alpha, e);
+        }
     }
 }
 
@@ -218,12 +205,14 @@ int64_t build_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape,
         total += n;
         const int b = 63 - __builtin_clzll((unsigned long long)n);
         int64_t T = shape.tile_elems[b] > 0 ? shape.tile_elems[b] : n;
-        T = std::min<int64_t>(T, 1 << 30);
+        T = std::min<int64_t>(T, kMaxTileElems);
+        const uint32_t ul = (uint32_t)std::min<int>(2, std::max<int>(0, shape.unroll_log2[b])) << 30;
         for (int64_t b0 = 0; b0 < n; b0 += T)
-            out->push_back(TileRec{b0, (int32_t)s, (int32_t)std::min<int64_t>(T, n - b0)});
+            out->push_back(TileRec{b0, (int32_t)s, (uint32_t)std::min<int64_t>(T, n - b0) | ul});
     }
-    std::stable_sort(out->begin(), out->end(),
-                     [](const TileRec &a, const TileRec &b) { return a.len > b.len; });
+    std::stable_sort(out->begin(), out->end(), [](const TileRec &a, const TileRec &b) {
+        return (a.len_ul & kLenMask) > (b.len_ul & kLenMask);
+    });
     return total;
 }
 
@@ -255,7 +244,6 @@ SegParams params_of(const wxpy_batch_plan *p, const wxpy_desc *dev_table) {
     sp.tiles = p->d_tiles;
     sp.ntiles = p->ntiles;
     sp.status = p->d_status;
-    std::memcpy(sp.unroll_log2, p->shape.unroll_log2, sizeof sp.unroll_log2);
     return sp;
 }
 
@@ -411,7 +399,6 @@ int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t 
         sp.tiles = d_tiles;
         sp.ntiles = (int64_t)tiles.size();
         sp.status = (unsigned *)buf;
-        std::memcpy(sp.unroll_log2, shape.unroll_log2, sizeof sp.unroll_log2);
         const int64_t wpb = shape.threads / 32;
         const unsigned grid = (unsigned)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)shape.blocks_per_sm * dp->sm_count,
@@ -563,7 +550,6 @@ int run_shape(SynthBatch &sb, const BatchShape &shape, const DeviceProps &dp, in
     sp.tiles = (const TileRec *)sb.tiles.p;
     sp.ntiles = ntiles;
     sp.status = (unsigned *)sb.status.p;
-    std::memcpy(sp.unroll_log2, shape.unroll_log2, sizeof sp.unroll_log2);
     // verification run on a poisoned output
     cudaError_t e = cudaMemsetAsync(sb.w.p, 0xff, (size_t)sb.slots * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sb.count.p, 0, 8, s);
@@ -628,7 +614,7 @@ int batch_tune_impl(int bmin, int bmax, unsigned flags, wxpy_batch_tune_result *
         int8_t best_u = shape.unroll_log2[b];
         for (int32_t T : kTiles) {
             if (T != 0 && T >= ((int64_t)2 << b)) continue;  // no cut: same as whole segment
-            for (int8_t ul = 0; ul < 4; ++ul) {
+            for (int8_t ul = 0; ul < 3; ++ul) {
                 if (quick && (ul == 0 || (T != 0 && T != 8192))) continue;
                 BatchShape cand = shape;
                 cand.tile_elems[b] = T;
@@ -716,8 +702,8 @@ extern "C" int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll) {
     if (bucket < 0 || bucket >= wx::kBuckets) return wx::fail(WXPY_EINVAL, "bad bucket %d", bucket);
     if (tile_elems < 0 || (tile_elems % 32) != 0 || tile_elems > (1 << 30))
         return wx::fail(WXPY_EINVAL, "tile length must be 0 or a multiple of 32 up to 2^30");
-    int ul = unroll == 1 ? 0 : unroll == 2 ? 1 : unroll == 4 ? 2 : unroll == 8 ? 3 : -1;
-    if (ul < 0) return wx::fail(WXPY_EINVAL, "unroll must be 1, 2, 4 or 8");
+    int ul = unroll == 1 ? 0 : unroll == 2 ? 1 : unroll == 4 ? 2 : -1;
+    if (ul < 0) return wx::fail(WXPY_EINVAL, "unroll must be 1, 2 or 4");
     wx::BatchShape s = wx::current_batch_shape();
     s.tile_elems[bucket] = tile_elems;
     s.unroll_log2[bucket] = (int8_t)ul;

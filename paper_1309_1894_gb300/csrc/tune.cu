@@ -423,7 +423,7 @@ int cache_load(const char *path, const char *expect_device) {
             long long b = -1, tile = -1, ul = -1;
             if (r == std::string::npos || !find_int(s, q, r, "bucket", &b) ||
                 !find_int(s, q, r, "tile", &tile) || !find_int(s, q, r, "unroll_log2", &ul) ||
-                b < 0 || b >= kBuckets || tile < 0 || tile > (1 << 30) || (tile % 32) || ul < 0 || ul > 3)
+                b < 0 || b >= kBuckets || tile < 0 || tile > (1 << 30) || (tile % 32) || ul < 0 || ul > 2)
                 return fail(WXPY_EINVAL, "%s: malformed batch entry", path);
             bs.tile_elems[b] = (int32_t)tile;
             bs.unroll_log2[b] = (int8_t)ul;

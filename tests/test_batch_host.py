@@ -46,11 +46,11 @@ def test_shape_table():
     wx.wxpy_batch_shape_reset()
     t0, u0 = wx.wxpy_batch_shape_get(20)
     assert t0 % 32 == 0 and u0 in (1, 2, 4, 8)
-    wx.wxpy_batch_shape_set(20, 4096, 8)
-    assert wx.wxpy_batch_shape_get(20) == (4096, 8)
+    wx.wxpy_batch_shape_set(20, 4096, 4)
+    assert wx.wxpy_batch_shape_get(20) == (4096, 4)
     wx.wxpy_batch_shape_set(3, 0, 1)
     assert wx.wxpy_batch_shape_get(3) == (0, 1)
-    for bad in ((20, 100, 4), (20, 4096, 3), (64, 0, 1), (-1, 0, 1)):
+    for bad in ((20, 100, 4), (20, 4096, 3), (20, 4096, 8), (64, 0, 1), (-1, 0, 1)):
         with pytest.raises(wx.WxpyError):
             wx.wxpy_batch_shape_set(*bad)
     wx.wxpy_batch_shape_reset()
@@ -63,13 +63,13 @@ def test_cache_file_with_batch_shapes(tmp_path):
     doc = {"format": "wxpy-tune-1", "device": "X",
            "batch_launch": {"threads": 256, "blocks_per_sm": 8},
            "batch": [{"bucket": 5, "tile": 0, "unroll_log2": 1},
-                     {"bucket": 18, "tile": 16384, "unroll_log2": 3}],
+                     {"bucket": 18, "tile": 16384, "unroll_log2": 2}],
            "entries": [{"key": 100, "variant": 42}]}
     p = tmp_path / "c.json"
     p.write_text(json.dumps(doc))
     wx.wxpy_tune_clear()
     wx.wxpy_tune_cache_load(str(p), check_device=False)
-    assert wx.wxpy_batch_shape_get(18) == (16384, 8)
+    assert wx.wxpy_batch_shape_get(18) == (16384, 4)
     assert wx.wxpy_batch_shape_get(5) == (0, 2)
     assert wx.wxpy_tune_get(100) == 42
     doc["batch"][0]["tile"] = 33  # not a multiple of 32: whole file refused
