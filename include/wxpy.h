@@ -237,6 +237,29 @@ int wxpy_batch_plan_destroy(wxpy_batch_plan *plan);
 int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t count,
                void *stream);
 
+/* The batched launch for callers that cannot allocate device memory: code
+ * whose device memory all belongs to another allocator (a framework's caching
+ * pool, a server's fixed arena) that must not see a cudaMalloc it did not
+ * make, and hot loops that cannot afford an allocation call.  The paper has
+ * no counterpart; this is a library convenience.
+ *
+ * Same results as wxpy_batch() for the problems in `dev_table` (a DEVICE
+ * table of `count` descriptors, owned by the caller, as are all vectors).  It
+ * calls no cudaMalloc, cudaFree or other allocating routine and takes no host
+ * table: the tiles are planned on the device, in `stream`, into a fixed
+ * scratch array of about 3 MiB that is a static device variable of the
+ * library, held by every GPU that loads the library until the process exits.
+ * Limit: count <= 65536 (WXPY_EINVAL above it, before anything is launched).
+ * The first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress) once for that device; make that first call before
+ * any stream capture.  Every call shares the one scratch array, which keeps
+ * the last call's contents (each call rebuilds what it reads): calls that
+ * overlap on the GPU -- on different streams, or from different threads --
+ * race on it and must be serialised by the caller.  Descriptors are checked on
+ * the device only for n <= 0 and for null or misaligned pointers (such
+ * problems are skipped); the caller guarantees that the problems are
+ * independent.  Asynchronous on `stream`. */
+int wxpy_batch_noalloc(const wxpy_desc *dev_table, int64_t count, void *stream);
 
 /* ---- the empirical search (Sec. 2) and its persisted results ------------------ */
 

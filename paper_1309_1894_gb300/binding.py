@@ -113,6 +113,7 @@ SIGNATURES = {
     "wxpy_batch_shape_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_batch_shape_reset": (_INT, []),
+    "wxpy_batch_noalloc": (_INT, [_P, _I64, _P]),
 }
 
 _lock = threading.Lock()
@@ -390,6 +391,12 @@ def wxpy_batch_plan_create(host_table) -> BatchPlan:
 def wxpy_batch(host_table, dev_table, stream=None) -> None:
     check(lib().wxpy_batch(_tptr(host_table), dev_table.data_ptr() if len(host_table) else 0,
                            len(host_table), _stream_handle(stream)), "wxpy_batch")
+
+
+def wxpy_batch_noalloc(dev_table, count: int, stream=None) -> None:
+    """The batched launch without any allocation (fixed library scratch; see wxpy.h)."""
+    check(lib().wxpy_batch_noalloc(dev_table.data_ptr() if count else 0, count,
+                                   _stream_handle(stream)), "wxpy_batch_noalloc")
 
 
 def wxpy_batch_tune(bucket_min: int, bucket_max: int, flags: int = 0) -> dict:
