@@ -401,6 +401,8 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
         result["batched"] = measure_batched(wx, lib, torch, dev, sh, stream, peak)
+        if args.serve_seconds > 0:
+            result["served"] = measure_served(args.serve_seconds)
     if rank == 0:
         rate1, passes, dt = cpu_oracle_rate(24, args.cpu_seconds, threads=1)
         cores = host_cores()
@@ -607,6 +609,37 @@ def measure_batched(wx, lib, torch, dev, sh, stream, peak, reps=20, per_call_rep
                                   for r in tune["buckets"]}}}
 
 
+SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)
+
+
+def measure_served(seconds):
+    """Poisson arrivals at five rates from 1e3 to 1e6 requests/s, n log-uniform in
+    [2^8, 2^24], alpha ~ U(-2,2), a 16 GiB admission budget, each rate for
+    ``seconds``: the continuous-batching server against the same server
+    launching every request call by call (serial baseline)."""
+    from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL
+    from paper_1309_1894_gb300 import synth
+    out = {"budget_gib": 16, "n_range": [1 << 8, 1 << 24], "seconds_per_rate": seconds,
+           "rates": list(SERVE_RATES), "batched": [], "serial": []}
+    for name, mode in (("batched", SERVE_BATCHED), ("serial", SERVE_SERIAL)):
+        with Server(budget_bytes=16 << 30, max_slots=4096, n_streams=2, max_batch=1024,
+                    max_queue=65536, mode=mode) as sv:
+            for i, rate in enumerate(SERVE_RATES):
+                r = sv.loadgen(rate=rate, duration_s=seconds, n_min=1 << 8, n_max=1 << 24,
+                               seed=synth.BASE_SEED + 100 + i, drain_timeout_s=120.0,
+                               check_drain=False)
+                out[name].append({
+                    "rate": rate, "offered": r["offered"], "completed": r["completed"],
+                    "rejected": r["rejected"], "failed": r["failed"],
+                    "p50_ms": r["p50_s"] * 1e3, "p99_ms": r["p99_s"] * 1e3,
+                    "max_ms": r["max_s"] * 1e3, "elem_per_s": r["elem_per_s"],
+                    "gbs": r["gbs"], "completed_per_s": r["completed"] / r["wall_s"],
+                    "max_queue": r["max_queue"], "backlog_at_end": r["backlog_at_end"],
+                    "mean_batch": r["mean_batch"], "launches": r["launches"],
+                    "drained": bool(r["drained"])})
+    return out
+
+
 def measure_streams(wx, lib, torch, dev, sh, stream, peak, reps=50, warm=10):
     """n = 2^30 (8 GiB per vector) split over 1, 2, 4, 8 streams: GB/s over
     ``reps`` back-to-back calls (each 24 GiB, far larger than L2)."""
@@ -655,9 +688,13 @@ def main():
                     help="time the built-in default variant instead of tuning first")
     ap.add_argument("--tune-cache", default=None,
                     help="load the tuned cells from this file if it exists, else tune and save")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of Poisson load per rate for the served leg (0 skips it)")
     ap.add_argument("--single", type=int, default=0,
                     help="profiling mode: only run wxpy() on n = SINGLE, --reps times")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="profiling mode: force this variant id instead of the tuned one")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -679,7 +716,9 @@ def run_single(args):
     wx.wxpy_fill_uniform(x, synth.BASE_SEED, synth.TAG_X)
     wx.wxpy_fill_uniform(y, synth.BASE_SEED, synth.TAG_Y)
     tuning = None
-    if args.tune_cache and os.path.exists(args.tune_cache):
+    if args.variant >= 0:
+        wx.wxpy_set_variant(args.variant)
+    elif args.tune_cache and os.path.exists(args.tune_cache):
         wx.wxpy_tune_cache_load(args.tune_cache, check_device=True)
     elif not args.no_tune:
         tuning = wx.wxpy_tune(n, 0)

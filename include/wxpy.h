@@ -354,6 +354,115 @@ int wxpy_batch_shape_get(int bucket, int *tile_elems, int *unroll);
 int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll);
 int wxpy_batch_shape_reset(void);
 
+/* ---- serving: continuous batching of wxpy requests --------------------------- */
+
+/* The paper has no serving layer; this runs the operation of Sec. 3 / Fig. 1
+ * for a stream of independent requests.  Each request (n, alpha, seed) gets
+ * inputs x, y = U(-1,1) streams (seed, WXPY_TAG_X) and (seed, WXPY_TAG_Y) of
+ * the seeded generator (wxpy_fill_uniform), filled on the device when the
+ * request is admitted, and result w = RN(RN(alpha*x) + y) -- the same bits
+ * whether it runs alone or batched with any other requests. */
+enum { WXPY_SERVE_BATCHED = 0, WXPY_SERVE_SERIAL = 1 };
+enum {
+    WXPY_REQ_QUEUED = 0,    /* waiting for memory or a slot */
+    WXPY_REQ_ADMITTED = 1,  /* buffers assigned, not yet launched */
+    WXPY_REQ_RUNNING = 2,   /* part of a batch in flight */
+    WXPY_REQ_DONE = 3,      /* result resident until released */
+    WXPY_REQ_FAILED = 4     /* its batch failed to launch or run */
+};
+
+typedef struct wxpy_server_config {
+    int64_t budget_bytes; /* device memory for request buffers (x, y, w of every
+                             resident request: 3 * 8n bytes rounded to 256 each),
+                             allocated once at create */
+    int32_t max_slots;    /* requests resident at once (admitted, not released) */
+    int32_t n_streams;    /* streams the batches run on, 1..16; batches on
+                             different streams overlap on the device */
+    int32_t max_batch;    /* requests coalesced into one batched launch */
+    int32_t max_queue;    /* queued requests beyond which submit refuses (EBUSY) */
+    int32_t mode;         /* WXPY_SERVE_BATCHED: fill + one segmented launch per
+                             batch; WXPY_SERVE_SERIAL: per-request launches, the
+                             baseline */
+    int32_t reserved;
+} wxpy_server_config;
+
+typedef struct wxpy_server wxpy_server; /* opaque */
+
+typedef struct wxpy_server_stats {
+    int64_t submitted, rejected, completed, failed;
+    int64_t queued_now, resident_now, max_queue;
+    int64_t batches, launches, elements_done, arena_used;
+    double mean_batch;   /* requests per batch */
+    double window_s;     /* time since the statistics were last reset */
+    double p50_s, p99_s, mean_s, max_s; /* submit -> completion, completed requests */
+} wxpy_server_stats;
+
+/* Allocates the arena (cudaMalloc of budget_bytes), per-stream staging, and
+ * starts the scheduler thread on the current device.  It admits requests in
+ * arrival order while memory and slots allow; it coalesces the admitted
+ * requests into one batch per free stream; it polls completion events.
+ * WXPY_EINVAL for a bad configuration, WXPY_ENOMEM, WXPY_ECUDA. */
+int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out);
+
+/* Queues a request; *ticket identifies it.  Never blocks.  WXPY_EBUDGET if it
+ * can never fit the budget, WXPY_EBUSY if the queue is full (counted as a
+ * reject), WXPY_EINVAL for n <= 0. */
+int wxpy_server_submit(wxpy_server *sv, int64_t n, double alpha, uint64_t seed,
+                       uint64_t *ticket);
+
+/* State (WXPY_REQ_*) and, once done or failed, the submit -> completion
+ * latency in seconds (-1 before).  WXPY_ENOTFOUND for an unknown or released
+ * ticket. */
+int wxpy_server_poll(wxpy_server *sv, uint64_t ticket, int *state, double *latency_s);
+
+/* Blocks until the request is done (WXPY_OK), failed (WXPY_ECUDA) or the
+ * timeout passes (WXPY_ETIMEOUT). */
+int wxpy_server_wait(wxpy_server *sv, uint64_t ticket, double timeout_s, double *latency_s);
+
+/* Device pointers of a done request's x, y, w and its n; valid until release. */
+int wxpy_server_result(wxpy_server *sv, uint64_t ticket, const double **x, const double **y,
+                       const double **w, int64_t *n);
+
+/* Frees a done or failed request's buffers and slot (WXPY_EBUSY while in flight). */
+int wxpy_server_release(wxpy_server *sv, uint64_t ticket);
+
+/* Counters and latency percentiles since the last reset; reset != 0 starts a
+ * new window. */
+int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out);
+
+/* Stops the scheduler after the batches in flight finish, frees everything.
+ * Requests not yet finished are dropped.  NULL is a no-op. */
+int wxpy_server_destroy(wxpy_server *sv);
+
+typedef struct wxpy_loadgen_config {
+    double rate;            /* Poisson arrival rate, requests per second */
+    double duration_s;      /* arrivals stop after this */
+    int64_t n_min, n_max;   /* request lengths log-uniform on [n_min, n_max] */
+    uint64_t seed;          /* arrival gaps, lengths, alphas and request seeds */
+    double drain_timeout_s; /* bound on the wait for accepted requests to finish */
+} wxpy_loadgen_config;
+
+typedef struct wxpy_loadgen_result {
+    int64_t offered, submitted, rejected, completed, failed;
+    int64_t max_queue, backlog_at_end, launches;
+    double p50_s, p99_s, mean_s, max_s; /* latency of the completed requests */
+    double wall_s;                      /* first arrival -> last completion */
+    double arrivals_s;                  /* span of the arrivals */
+    double elem_per_s, gbs;             /* completed elements (24 B each) / wall_s */
+    double mean_batch;
+    int32_t drained, reserved;
+} wxpy_loadgen_result;
+
+/* A built-in open-loop client.  It submits requests at Poisson arrival times
+ * for duration_s, with lengths and alphas drawn from the seeded generator.
+ * Its requests release their buffers as soon as they complete, and requests
+ * refused at submit count as rejects.  It then waits, up to drain_timeout_s,
+ * for the accepted requests to finish.  Blocking.  Resets the statistics
+ * window.  WXPY_ETIMEOUT if the load did not drain (the result still holds
+ * what was measured). */
+int wxpy_server_loadgen(wxpy_server *sv, const wxpy_loadgen_config *cfg,
+                        wxpy_loadgen_result *out);
+
 /* ---- seeded synthetic inputs ----------------------------------------------------- */
 
 /* Stream tags used by the library's own synthetic inputs (server requests). */

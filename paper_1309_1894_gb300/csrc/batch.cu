@@ -22,16 +22,10 @@
 #include <vector>
 
 #include "internal.h"
+#include "seg_tile.cuh"
 
 namespace wx {
 
-struct TileRec {
-    int64_t begin;     // first element of the tile within its segment
-    int32_t seg;       // segment index in the descriptor table
-    uint32_t len_ul;   // bits 0..29: elements in the tile; bits 30..31: log2 unroll
-};
-constexpr uint32_t kLenMask = (1u << 30) - 1;
-constexpr int64_t kMaxTileElems = (1 << 30) - 32;
 static_assert(sizeof(TileRec) == 16, "tile records are 16 bytes");
 static_assert(sizeof(wxpy_desc) == 40, "descriptor layout");
 
@@ -41,50 +35,6 @@ struct SegParams {
     int64_t ntiles;
     unsigned *status;  // bit 0: a tile exceeded its descriptor's n
 };
-
-namespace {
-
-// One pass: up to kMaxU 32-byte vectors of x and y per lane -- the tile's
-// unroll U decides how many -- all loads issued before any store.  The unroll
-// is a run-time predicate on one fixed-size body, so a single body serves
-// every bucket; a body per (width, unroll) behind a switch made the compiler
-// spill.
-constexpr int kMaxU = 4;
-
-__device__ __forceinline__ void seg_body4(const double *x, const double *y, double *w,
-                                          double alpha, int64_t nch, int lane, int U) {
-    const int64_t step = 32 * U;
-    for (int64_t c0 = lane; c0 < nch; c0 += step) {
-        double xv[kMaxU][4], yv[kMaxU][4], wv[kMaxU][4];
-#pragma unroll
-        for (int u = 0; u < kMaxU; ++u) {
-            const int64_t c = c0 + 32 * u;
-            if (u < U && c < nch) {
-                ld_vec<4, 2>(x + c * 4, xv[u]);
-                ld_vec<4, 2>(y + c * 4, yv[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kMaxU; ++u) {
-            const int64_t c = c0 + 32 * u;
-            if (u < U && c < nch) {
-                wxpy_vec<4>(alpha, xv[u], yv[u], wv[u]);
-                st_vec<4, 2>(w + c * 4, wv[u]);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void scalar_op(const double *x, const double *y, double *w,
-                                          double alpha, int64_t e) {
-    double xv[1], yv[1], wv[1];
-    ld_vec<1, 2>(x + e, xv);
-    ld_vec<1, 2>(y + e, yv);
-    wxpy_vec<1>(alpha, xv, yv, wv);
-    st_vec<1, 2>(w + e, wv);
-}
-
-}  // namespace
 
 __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
     const int lane = threadIdx.x & 31;
@@ -98,25 +48,8 @@ __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
             if (lane == 0) atomicOr(p.status, 1u);
             continue;
         }
-        const double *x = d.x + r.begin;
-        const double *y = d.y + r.begin;
-        double *w = d.w + r.begin;
-        const uintptr_t ax = (uintptr_t)x, ay = (uintptr_t)y, aw = (uintptr_t)w;
-        if ((((ax ^ aw) | (ay ^ aw)) & 31u) == 0) {
-            // x, y, w share their offset mod 32 bytes: peel to the boundary,
-            // stream 32-byte vectors, finish the tail.
-            const int64_t head = min(len, (int64_t)((4 - (int)((aw >> 3) & 3)) & 3));
-            const int64_t nch = (len - head) / 4;
-            const int64_t body_end = head + nch * 4;
-            if (lane < head) scalar_op(x, y, w, d.alpha, lane);
-            if (lane >= 4 && body_end + (lane - 4) < len)
-                scalar_op(x, y, w, d.alpha, body_end + (lane - 4));
-            seg_body4(x + head, y + head, w + head, d.alpha, nch, lane, 1 << (r.len_ul >> 30));
-        } else {
-            // Pointers that share less than 32-byte alignment (rare: separate
-            // allocations are 256-byte aligned): coalesced 8-byte accesses.
-            for (int64_t e = lane; e < len; e += 32) scalar_op(x, y, w, d.alpha, e);
-        }
+        tile_wxpy(d.x + r.begin, d.y + r.begin, d.w + r.begin, d.alpha, len, lane,
+                  1 << (r.len_ul >> 30));
     }
 }
 
@@ -214,6 +147,24 @@ int64_t build_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape,
         return (a.len_ul & kLenMask) > (b.len_ul & kLenMask);
     });
     return total;
+}
+
+cudaError_t launch_segmented(const wxpy_desc *dev_table, const TileRec *tiles, int64_t ntiles,
+                             unsigned *status, const BatchShape &shape, int sm_count,
+                             cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    const int64_t wpb = shape.threads / 32;
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)shape.blocks_per_sm * sm_count, (ntiles + wpb - 1) / wpb));
+    cudaError_t e = injected_launch_error();
+    if (e != cudaSuccess) return e;
+    SegParams sp;
+    sp.table = dev_table;
+    sp.tiles = tiles;
+    sp.ntiles = ntiles;
+    sp.status = status;
+    wxpy_seg_kernel<<<grid, shape.threads, 0, s>>>(sp);
+    return cudaGetLastError();
 }
 
 }  // namespace wx

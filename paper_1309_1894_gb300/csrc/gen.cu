@@ -11,21 +11,12 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "gen.cuh"
 #include "internal.h"
 
 namespace wx {
 
-constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
-
-__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-uint64_t stream_key(uint64_t seed, uint32_t tag) {
-    return mix64(seed + ((uint64_t)tag + 1) * kGolden);
-}
+uint64_t stream_key(uint64_t seed, uint32_t tag) { return stream_key_of(seed, tag); }
 
 // dst[i] = lo + width * u(start + i).  lo + width*u is computed as two
 // correctly rounded operations; for the ranges the library uses (width a power

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "wxpy.h"
 #include "single_kernel.cuh"
@@ -76,6 +77,14 @@ int run_variant(const Variant &v, const CallClass &c, int64_t n, double alpha,
 cudaError_t injected_launch_error();
 
 // ---- batched launch (batch.cu) ----
+// One work item of the segmented launch.
+struct TileRec {
+    int64_t begin;    // first element of the tile within its segment
+    int32_t seg;      // segment index in the descriptor table
+    uint32_t len_ul;  // bits 0..29: elements in the tile; bits 30..31: log2 unroll
+};
+constexpr uint32_t kLenMask = (1u << 30) - 1;
+constexpr int64_t kMaxTileElems = (1 << 30) - 32;
 struct BatchShape {
     int threads;                   // block size of the persistent kernel
     int blocks_per_sm;             // grid = blocks_per_sm * sm_count (capped by tiles)
@@ -86,6 +95,13 @@ BatchShape default_batch_shape();
 BatchShape current_batch_shape();
 void set_batch_shape(const BatchShape &s);
 int validate_table(const wxpy_desc *t, int64_t count);
+// Tile list of a validated table (largest first); returns the element total.
+int64_t build_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape,
+                    std::vector<TileRec> *out);
+// One launch of the segmented kernel over `ntiles` device tile records.
+cudaError_t launch_segmented(const wxpy_desc *dev_table, const TileRec *tiles, int64_t ntiles,
+                             unsigned *status, const BatchShape &shape, int sm_count,
+                             cudaStream_t s);
 
 // tune.cu: loads $WXPY_TUNE_CACHE once per process (errors ignored).
 void autoload_tune_cache();

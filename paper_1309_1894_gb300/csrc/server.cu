@@ -1,0 +1,713 @@
+// server.cu -- a continuous-batching request server for VecWXPY.
+//
+// Clients submit requests (n, alpha, seed).  A scheduler thread
+//   1. admits queued requests in arrival order while the device-memory budget
+//      (one arena, first fit, 256-byte blocks holding x, y, w) and the slot
+//      limit allow -- a request waits, it is never reordered past;
+//   2. coalesces every admitted, not yet launched request (up to max_batch)
+//      into one batch and launches it on the next free stream: a segmented
+//      fill of the inputs from the request seeds, then the segmented WXPY
+//      kernel over the same tile list -- two launches per batch, whatever the
+//      number of requests in it;
+//   3. polls the batches' completion events, stamps each request's completion
+//      time, and frees the buffers of requests marked auto-release.
+// Requests that arrive while batches run on other streams are admitted and
+// launched as soon as memory and a stream free up, so their work overlaps on
+// the device (continuous batching, not a queue drained batch by batch).  The
+// serial mode is the baseline: the same steps per request with per-call
+// launches (fill x, fill y, wxpy()) and no coalescing.
+//
+// Each request's result is element-wise w = RN(RN(alpha*x) + y) on its own
+// inputs x, y = U(-1,1) streams (seed, 1) and (seed, 2) (paper Sec. 3, Fig. 1
+// vecwxpy), so it is the same bits alone and in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gen.cuh"
+#include "internal.h"
+#include "seg_tile.cuh"
+
+namespace wx {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds(Clock::duration d) { return std::chrono::duration<double>(d).count(); }
+
+constexpr int64_t kBlock = 256;  // arena granularity (bytes)
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// First-fit allocator over [0, size) with coalescing of freed blocks.
+class Arena {
+  public:
+    void init(int64_t size) {
+        free_.clear();
+        size_ = size / kBlock * kBlock;
+        if (size_ > 0) free_[0] = size_;
+        used_ = 0;
+    }
+    int64_t alloc(int64_t bytes) {
+        bytes = round_up(bytes, kBlock);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const int64_t off = it->first, rem = it->second - bytes;
+            free_.erase(it);
+            if (rem) free_[off + bytes] = rem;
+            used_ += bytes;
+            return off;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t bytes) {
+        bytes = round_up(bytes, kBlock);
+        used_ -= bytes;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    int64_t used() const { return used_; }
+    int64_t size() const { return size_; }
+
+  private:
+    std::map<int64_t, int64_t> free_;
+    int64_t size_ = 0, used_ = 0;
+};
+
+enum ReqState { kQueued = 0, kAdmitted = 1, kRunning = 2, kDone = 3, kFailed = 4 };
+
+struct Request {
+    int64_t n = 0;
+    double alpha = 0;
+    uint64_t seed = 0;
+    int state = kQueued;
+    bool auto_release = false;
+    int64_t off = -1, bytes = 0;
+    double *x = nullptr, *y = nullptr, *w = nullptr;
+    Clock::time_point t_submit, t_done;
+    int error = 0;
+};
+
+// Per request of a batch: where its tiles start in the batch's tile numbering,
+// its tile length and unroll.  The host writes only this (24 bytes per
+// request); warps find their request by binary search over first_tile, so no
+// per-tile list is built on the host however many tiles a batch has.
+struct ServePlan {
+    int64_t first_tile;  // exclusive prefix of tile counts over the batch
+    int64_t tile_len;    // elements per tile
+    int32_t ulog;        // log2 of the unroll
+    int32_t pad;
+};
+
+// A batch in flight on one stream, with its staging (pinned host) and device tables.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+    int64_t cap_segs = 0;
+    wxpy_desc *h_table = nullptr, *d_table = nullptr;
+    uint64_t *h_seeds = nullptr, *d_seeds = nullptr;
+    ServePlan *h_plan = nullptr, *d_plan = nullptr;
+};
+
+// Largest s in [lo, count) with plan[s].first_tile <= t (tiles only grow
+// along a warp's sequence, so the previous answer is a valid lower bound).
+__device__ __forceinline__ int64_t find_request(const ServePlan *plan, int64_t count, int64_t t,
+                                                int64_t lo) {
+    int64_t hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (plan[mid].first_tile <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Generates x and y of every request of a batch, tile by tile.
+__global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
+                                                         const uint64_t *seeds,
+                                                         const ServePlan *plan, int64_t count,
+                                                         int64_t ntiles) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t s = 0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        s = find_request(plan, count, t, s);
+        const wxpy_desc d = table[s];
+        const ServePlan sp = plan[s];
+        const int64_t begin = (t - sp.first_tile) * sp.tile_len;
+        const int64_t end = min(d.n, begin + sp.tile_len);
+        const uint64_t kx = stream_key_of(seeds[s], 1), ky = stream_key_of(seeds[s], 2);
+        double *x = const_cast<double *>(d.x), *y = const_cast<double *>(d.y);
+        for (int64_t i = begin + lane; i < end; i += 32) {
+            x[i] = uniform_pm1(kx, i);
+            y[i] = uniform_pm1(ky, i);
+        }
+    }
+}
+
+// w = RN(RN(alpha*x) + y) for every request of a batch, tile by tile.
+__global__ void __launch_bounds__(256, 2) serve_wxpy_kernel(const wxpy_desc *table,
+                                                            const ServePlan *plan, int64_t count,
+                                                            int64_t ntiles) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t s = 0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        s = find_request(plan, count, t, s);
+        const wxpy_desc d = table[s];
+        const ServePlan sp = plan[s];
+        const int64_t begin = (t - sp.first_tile) * sp.tile_len;
+        const int64_t len = min(sp.tile_len, d.n - begin);
+        if (len > 0) tile_wxpy(d.x + begin, d.y + begin, d.w + begin, d.alpha, len, lane, 1 << sp.ulog);
+    }
+}
+
+}  // namespace
+}  // namespace wx
+
+using namespace wx;
+
+struct wxpy_server {
+    wxpy_server_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    char *arena_base = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    int next_slot = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_submit;  // wakes the scheduler
+    std::condition_variable cv_done;    // wakes waiters
+    std::deque<uint64_t> queue;
+    std::vector<uint64_t> admitted;
+    std::unordered_map<uint64_t, Request> reqs;
+    uint64_t next_ticket = 1;
+    int64_t resident = 0;
+
+    // statistics since the last reset
+    Clock::time_point t_reset;
+    int64_t submitted = 0, rejected = 0, completed = 0, failed = 0, max_queue = 0;
+    int64_t batches = 0, launches = 0, elements_done = 0, requests_launched = 0;
+    std::vector<double> latencies;
+
+    std::thread sched;
+    std::atomic<bool> stop{false};
+    int sched_error = 0;
+};
+
+namespace wx {
+namespace {
+
+void free_slot(Slot &s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.d_table) cudaFree(s.d_table);
+    if (s.d_seeds) cudaFree(s.d_seeds);
+    if (s.d_plan) cudaFree(s.d_plan);
+    if (s.h_table) cudaFreeHost(s.h_table);
+    if (s.h_seeds) cudaFreeHost(s.h_seeds);
+    if (s.h_plan) cudaFreeHost(s.h_plan);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot{};
+}
+
+cudaError_t init_slot(Slot &s, int64_t segs) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_table, sizeof(wxpy_desc) * segs);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_seeds, sizeof(uint64_t) * segs);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_plan, sizeof(ServePlan) * segs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_table, sizeof(wxpy_desc) * segs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_seeds, sizeof(uint64_t) * segs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_plan, sizeof(ServePlan) * segs);
+    s.cap_segs = segs;
+    return e;
+}
+
+// Marks the requests of a finished (or failed) slot; caller holds the lock.
+void retire_slot(wxpy_server *sv, Slot &s, Clock::time_point now, int error) {
+    for (uint64_t t : s.tickets) {
+        auto it = sv->reqs.find(t);
+        if (it == sv->reqs.end()) continue;
+        Request &r = it->second;
+        r.t_done = now;
+        if (error) {
+            r.state = kFailed;
+            r.error = error;
+            ++sv->failed;
+        } else {
+            r.state = kDone;
+            ++sv->completed;
+            sv->elements_done += r.n;
+            sv->latencies.push_back(seconds(now - r.t_submit));
+        }
+        if (r.auto_release) {
+            if (r.off >= 0) sv->arena.release(r.off, r.bytes);
+            --sv->resident;
+            sv->reqs.erase(it);
+        }
+    }
+    s.tickets.clear();
+    s.busy = false;
+    sv->cv_done.notify_all();
+}
+
+// Launches the requests in `batch` on slot s.  Caller does NOT hold the lock;
+// the requests are already marked running.  Returns a cudaError_t.
+cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> &batch) {
+    cudaError_t e = cudaSuccess;
+    if (sv->cfg.mode == WXPY_SERVE_SERIAL) {
+        // Baseline: the same requests, launched call by call (three launches
+        // per request) instead of coalesced into two launches per batch.
+        for (Request *r : batch) {
+            int st = launch_fill_uniform(r->x, r->n, r->seed, 1, 0, -1.0, 1.0, s.stream);
+            if (st == WXPY_OK) st = launch_fill_uniform(r->y, r->n, r->seed, 2, 0, -1.0, 1.0, s.stream);
+            if (st == WXPY_OK) st = wxpy(r->n, r->alpha, r->x, r->y, r->w, s.stream);
+            if (st != WXPY_OK) return (cudaError_t)(wxpy_last_cuda_error() ? wxpy_last_cuda_error() : 1);
+            sv->launches += 3;
+        }
+        return cudaEventRecord(s.done, s.stream);
+    }
+    const int64_t count = (int64_t)batch.size();
+    const BatchShape shape = current_batch_shape();
+    int64_t ntiles = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const Request *r = batch[i];
+        s.h_table[i] = wxpy_desc{r->n, r->alpha, r->x, r->y, r->w};
+        s.h_seeds[i] = r->seed;
+        const int b = 63 - __builtin_clzll((unsigned long long)r->n);
+        const int64_t T = std::min<int64_t>(shape.tile_elems[b] > 0 ? shape.tile_elems[b] : r->n,
+                                            kMaxTileElems);
+        s.h_plan[i] = ServePlan{ntiles, T, std::min<int>(2, std::max<int>(0, shape.unroll_log2[b])), 0};
+        ntiles += (r->n + T - 1) / T;
+    }
+    e = cudaMemcpyAsync(s.d_table, s.h_table, sizeof(wxpy_desc) * count, cudaMemcpyHostToDevice,
+                        s.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_seeds, s.h_seeds, sizeof(uint64_t) * count, cudaMemcpyHostToDevice,
+                            s.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_plan, s.h_plan, sizeof(ServePlan) * count, cudaMemcpyHostToDevice,
+                            s.stream);
+    if (e != cudaSuccess) return e;
+    const int64_t wpb = 256 / 32;
+    const unsigned fill_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)8 * sv->sm_count, (ntiles + wpb - 1) / wpb));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)shape.blocks_per_sm * sv->sm_count, (ntiles + wpb - 1) / wpb));
+    e = injected_launch_error();
+    if (e != cudaSuccess) return e;
+    serve_fill_kernel<<<fill_grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
+                                                       ntiles);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    serve_wxpy_kernel<<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sv->launches += 2;
+    return cudaEventRecord(s.done, s.stream);
+}
+
+void scheduler(wxpy_server *sv) {
+    cudaSetDevice(sv->device);
+    std::vector<Request *> batch;
+    while (true) {
+        bool progress = false;
+        // 1. completions
+        for (Slot &s : sv->slots) {
+            if (!s.busy) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            const Clock::time_point now = Clock::now();
+            std::lock_guard<std::mutex> lk(sv->mu);
+            retire_slot(sv, s, now, q == cudaSuccess ? 0 : (int)q);
+            progress = true;
+        }
+        // 2. admission, in arrival order
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            while (!sv->queue.empty() && sv->resident < sv->cfg.max_slots) {
+                Request &r = sv->reqs[sv->queue.front()];
+                const int64_t vb = round_up(r.n * 8, kBlock);
+                const int64_t off = sv->arena.alloc(3 * vb);
+                if (off < 0) break;  // wait for memory; no reordering
+                r.off = off;
+                r.bytes = 3 * vb;
+                r.x = (double *)(sv->arena_base + off);
+                r.y = (double *)(sv->arena_base + off + vb);
+                r.w = (double *)(sv->arena_base + off + 2 * vb);
+                r.state = kAdmitted;
+                sv->admitted.push_back(sv->queue.front());
+                sv->queue.pop_front();
+                ++sv->resident;
+                progress = true;
+            }
+        }
+        // 3. launch the admitted requests on a free stream
+        Slot *free_slot_ptr = nullptr;
+        for (size_t k = 0; k < sv->slots.size(); ++k) {
+            Slot &s = sv->slots[(sv->next_slot + k) % sv->slots.size()];
+            if (!s.busy) {
+                free_slot_ptr = &s;
+                sv->next_slot = (int)((sv->next_slot + k + 1) % sv->slots.size());
+                break;
+            }
+        }
+        if (free_slot_ptr) {
+            Slot &s = *free_slot_ptr;
+            batch.clear();
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                const int64_t maxb = sv->cfg.max_batch;
+                size_t taken = 0;
+                for (; taken < sv->admitted.size() && (int64_t)taken < maxb &&
+                       (int64_t)taken < s.cap_segs;
+                     ++taken) {
+                    Request &r = sv->reqs[sv->admitted[taken]];
+                    r.state = kRunning;
+                    batch.push_back(&r);
+                    s.tickets.push_back(sv->admitted[taken]);
+                }
+                sv->admitted.erase(sv->admitted.begin(), sv->admitted.begin() + taken);
+                if (!batch.empty()) {
+                    s.busy = true;
+                    ++sv->batches;
+                    sv->requests_launched += (int64_t)batch.size();
+                }
+            }
+            if (!batch.empty()) {
+                const cudaError_t e = launch_batch(sv, s, batch);
+                progress = true;
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    // the stream may still hold part of the batch: let it drain
+                    cudaStreamSynchronize(s.stream);
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    retire_slot(sv, s, Clock::now(), (int)e);
+                }
+            }
+        }
+        if (sv->stop.load()) {
+            bool idle = true;
+            for (Slot &s : sv->slots) idle = idle && !s.busy;
+            if (idle) break;
+        }
+        if (!progress) {
+            bool inflight = false;
+            for (Slot &s : sv->slots) inflight = inflight || s.busy;
+            std::unique_lock<std::mutex> lk(sv->mu);
+            if (!inflight && !sv->stop.load() && sv->queue.empty() && sv->admitted.empty()) {
+                sv->cv_submit.wait_for(lk, std::chrono::milliseconds(2));
+            } else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(inflight ? 2 : 20));
+            }
+        }
+    }
+}
+
+int submit_locked(wxpy_server *sv, int64_t n, double alpha, uint64_t seed, bool auto_release,
+                  uint64_t *ticket) {
+    if (n <= 0) return fail(WXPY_EINVAL, "request needs n > 0");
+    const int64_t bytes = 3 * round_up(n * 8, kBlock);
+    if (n > (int64_t)1 << 40 || bytes > sv->arena.size())
+        return fail(WXPY_EBUDGET, "request of %lld elements needs %lld bytes, budget %lld",
+                    (long long)n, (long long)bytes, (long long)sv->arena.size());
+    if ((int64_t)sv->queue.size() >= sv->cfg.max_queue) {
+        ++sv->rejected;
+        return fail(WXPY_EBUSY, "admission queue full (%lld)", (long long)sv->cfg.max_queue);
+    }
+    const uint64_t t = sv->next_ticket++;
+    Request &r = sv->reqs[t];
+    r.n = n;
+    r.alpha = alpha;
+    r.seed = seed;
+    r.auto_release = auto_release;
+    r.t_submit = Clock::now();
+    sv->queue.push_back(t);
+    sv->max_queue = std::max<int64_t>(sv->max_queue, (int64_t)sv->queue.size());
+    ++sv->submitted;
+    *ticket = t;
+    return WXPY_OK;
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + (long)k, v.end());
+    return v[k];
+}
+
+}  // namespace
+}  // namespace wx
+
+extern "C" {
+
+int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out) {
+    if (!cfg || !out) return fail(WXPY_EINVAL, "null argument");
+    *out = nullptr;
+    if (cfg->budget_bytes < 3 * kBlock || cfg->max_slots < 1 || cfg->n_streams < 1 ||
+        cfg->n_streams > 16 || cfg->max_batch < 1 || cfg->max_queue < 1 ||
+        (cfg->mode != WXPY_SERVE_BATCHED && cfg->mode != WXPY_SERVE_SERIAL))
+        return fail(WXPY_EINVAL, "bad server configuration");
+    int st = WXPY_OK;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    auto *sv = new wxpy_server;
+    sv->cfg = *cfg;
+    sv->device = dp->device;
+    sv->sm_count = dp->sm_count;
+    cudaError_t e = cudaMalloc(&sv->arena_base, (size_t)cfg->budget_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete sv;
+        return fail(WXPY_ENOMEM, "server arena of %lld bytes", (long long)cfg->budget_bytes);
+    }
+    sv->arena.init(cfg->budget_bytes);
+    const int64_t segs = std::min<int64_t>(cfg->max_batch, cfg->max_slots);
+    sv->slots.resize((size_t)cfg->n_streams);
+    for (Slot &s : sv->slots) {
+        e = init_slot(s, segs);
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+        for (Slot &s : sv->slots) free_slot(s);
+        cudaFree(sv->arena_base);
+        delete sv;
+        return fail_cuda(e, "server stream/staging setup");
+    }
+    sv->t_reset = Clock::now();
+    sv->sched = std::thread(scheduler, sv);
+    *out = sv;
+    return WXPY_OK;
+}
+
+int wxpy_server_submit(wxpy_server *sv, int64_t n, double alpha, uint64_t seed, uint64_t *ticket) {
+    if (!sv || !ticket) return fail(WXPY_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int st = submit_locked(sv, n, alpha, seed, false, ticket);
+    if (st == WXPY_OK) sv->cv_submit.notify_one();
+    return st;
+}
+
+int wxpy_server_poll(wxpy_server *sv, uint64_t ticket, int *state, double *latency_s) {
+    if (!sv || !state) return fail(WXPY_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(WXPY_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    *state = it->second.state;
+    if (latency_s)
+        *latency_s = it->second.state >= kDone ? seconds(it->second.t_done - it->second.t_submit) : -1.0;
+    return WXPY_OK;
+}
+
+int wxpy_server_wait(wxpy_server *sv, uint64_t ticket, double timeout_s, double *latency_s) {
+    if (!sv) return fail(WXPY_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s));
+    while (true) {
+        auto it = sv->reqs.find(ticket);
+        if (it == sv->reqs.end()) return fail(WXPY_ENOTFOUND, "unknown ticket");
+        if (it->second.state >= kDone) {
+            if (latency_s) *latency_s = seconds(it->second.t_done - it->second.t_submit);
+            if (it->second.state == kFailed)
+                return fail(WXPY_ECUDA, "request failed with CUDA error %d", it->second.error);
+            return WXPY_OK;
+        }
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+            Clock::now() >= deadline)
+            return fail(WXPY_ETIMEOUT, "ticket %llu not done after %.3f s",
+                        (unsigned long long)ticket, timeout_s);
+    }
+}
+
+int wxpy_server_result(wxpy_server *sv, uint64_t ticket, const double **x, const double **y,
+                       const double **w, int64_t *n) {
+    if (!sv) return fail(WXPY_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(WXPY_ENOTFOUND, "unknown ticket");
+    const Request &r = it->second;
+    if (r.state != kDone) return fail(WXPY_EBUSY, "ticket not done (state %d)", r.state);
+    if (x) *x = r.x;
+    if (y) *y = r.y;
+    if (w) *w = r.w;
+    if (n) *n = r.n;
+    return WXPY_OK;
+}
+
+int wxpy_server_release(wxpy_server *sv, uint64_t ticket) {
+    if (!sv) return fail(WXPY_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(WXPY_ENOTFOUND, "unknown ticket");
+    if (it->second.state < kDone) return fail(WXPY_EBUSY, "ticket still in flight");
+    if (it->second.off >= 0) sv->arena.release(it->second.off, it->second.bytes);
+    --sv->resident;
+    sv->reqs.erase(it);
+    sv->cv_submit.notify_one();  // memory and a slot freed
+    return WXPY_OK;
+}
+
+int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
+    if (!sv || !out) return fail(WXPY_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::memset(out, 0, sizeof *out);
+    out->submitted = sv->submitted;
+    out->rejected = sv->rejected;
+    out->completed = sv->completed;
+    out->failed = sv->failed;
+    out->queued_now = (int64_t)sv->queue.size();
+    out->resident_now = sv->resident;
+    out->max_queue = sv->max_queue;
+    out->batches = sv->batches;
+    out->launches = sv->launches;
+    out->mean_batch = sv->batches ? (double)sv->requests_launched / (double)sv->batches : 0.0;
+    out->elements_done = sv->elements_done;
+    out->arena_used = sv->arena.used();
+    out->window_s = seconds(Clock::now() - sv->t_reset);
+    out->p50_s = percentile(sv->latencies, 0.50);
+    out->p99_s = percentile(sv->latencies, 0.99);
+    double sum = 0, mx = 0;
+    for (double v : sv->latencies) {
+        sum += v;
+        mx = std::max(mx, v);
+    }
+    out->mean_s = sv->latencies.empty() ? 0.0 : sum / (double)sv->latencies.size();
+    out->max_s = mx;
+    if (reset) {
+        sv->submitted = sv->rejected = sv->completed = sv->failed = 0;
+        sv->batches = sv->launches = sv->elements_done = sv->requests_launched = 0;
+        sv->max_queue = (int64_t)sv->queue.size();
+        sv->latencies.clear();
+        sv->t_reset = Clock::now();
+    }
+    return WXPY_OK;
+}
+
+int wxpy_server_destroy(wxpy_server *sv) {
+    if (!sv) return WXPY_OK;
+    sv->stop.store(true);
+    sv->cv_submit.notify_all();
+    if (sv->sched.joinable()) sv->sched.join();
+    for (Slot &s : sv->slots) free_slot(s);
+    if (sv->arena_base) cudaFree(sv->arena_base);
+    delete sv;
+    return WXPY_OK;
+}
+
+int wxpy_server_loadgen(wxpy_server *sv, const wxpy_loadgen_config *cfg, wxpy_loadgen_result *out) {
+    if (!sv || !cfg || !out) return fail(WXPY_EINVAL, "null argument");
+    if (!(cfg->rate > 0) || !(cfg->duration_s > 0) || cfg->n_min < 1 || cfg->n_max < cfg->n_min)
+        return fail(WXPY_EINVAL, "bad load configuration");
+    std::memset(out, 0, sizeof *out);
+    wxpy_server_stats dummy;
+    wxpy_server_get_stats(sv, 1, &dummy);  // start a fresh statistics window
+    // Arrival times, lengths and alphas from the counter-based generator.
+    auto u01 = [](uint64_t key, uint64_t i) {
+        return (double)(mix64(key + (i + 1) * kGolden) >> 11) * 0x1.0p-53;
+    };
+    const uint64_t k_gap = stream_key_of(cfg->seed, 5), k_len = stream_key_of(cfg->seed, 4),
+                   k_alpha = stream_key_of(cfg->seed, 3);
+    const double la = std::log2((double)cfg->n_min), lb = std::log2((double)cfg->n_max + 1.0);
+    const Clock::time_point t0 = Clock::now();
+    double t_next = 0.0;
+    int64_t offered = 0, accepted = 0, refused = 0;
+    std::vector<uint64_t> tickets;
+    for (uint64_t i = 0;; ++i) {
+        t_next += -std::log1p(-u01(k_gap, i)) / cfg->rate;
+        if (t_next > cfg->duration_s) break;
+        while (seconds(Clock::now() - t0) < t_next) {
+            const double ahead = t_next - seconds(Clock::now() - t0);
+            if (ahead > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        int64_t n = (int64_t)std::floor(std::exp2(la + u01(k_len, i) * (lb - la)));
+        n = std::min<int64_t>(std::max<int64_t>(n, cfg->n_min), cfg->n_max);
+        const double alpha = 4.0 * u01(k_alpha, i) - 2.0;
+        ++offered;
+        uint64_t t = 0;
+        int st;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            st = submit_locked(sv, n, alpha, cfg->seed + 1000003ull * (i + 1), true, &t);
+        }
+        if (st == WXPY_OK) {
+            ++accepted;
+            sv->cv_submit.notify_one();
+        } else {
+            ++refused;
+        }
+    }
+    const double arrivals_end = seconds(Clock::now() - t0);
+    int64_t backlog_end = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        backlog_end = (int64_t)sv->queue.size() + (int64_t)sv->admitted.size();
+    }
+    // Drain: wait (bounded) for every accepted request to finish.
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(cfg->drain_timeout_s));
+    bool drained = false;
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        while (true) {
+            if (sv->completed + sv->failed >= accepted) {
+                drained = true;
+                break;
+            }
+            if (Clock::now() >= deadline) break;
+            sv->cv_done.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+    const double wall = seconds(Clock::now() - t0);
+    wxpy_server_stats s;
+    wxpy_server_get_stats(sv, 0, &s);
+    out->offered = offered;
+    out->submitted = accepted;
+    out->rejected = refused;
+    out->completed = s.completed;
+    out->failed = s.failed;
+    out->p50_s = s.p50_s;
+    out->p99_s = s.p99_s;
+    out->mean_s = s.mean_s;
+    out->max_s = s.max_s;
+    out->wall_s = wall;
+    out->arrivals_s = arrivals_end;
+    out->elem_per_s = (double)s.elements_done / wall;
+    out->gbs = 24.0 * (double)s.elements_done / wall / 1e9;
+    out->max_queue = s.max_queue;
+    out->backlog_at_end = backlog_end;
+    out->mean_batch = s.mean_batch;
+    out->launches = s.launches;
+    out->drained = drained ? 1 : 0;
+    return drained ? WXPY_OK : fail(WXPY_ETIMEOUT, "load did not drain within %.1f s",
+                                    cfg->drain_timeout_s);
+}
+
+}  // extern "C"

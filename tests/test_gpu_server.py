@@ -1,0 +1,155 @@
+"""GPU tests of the continuous-batching server through the C ABI.
+
+Each request's result must be the same bits alone and in the mix (0 ULP):
+equal to a standalone wxpy() on the same seeded inputs, and to the oracle.
+The server's admission (budget, slots, queue limit), failure reporting and
+built-in Poisson client are checked too.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import synth
+from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL, REQ_DONE, \
+    REQ_QUEUED, REQ_FAILED
+
+pytestmark = pytest.mark.gpu
+
+
+def _from_ptr(ptr, n):
+    """A float64 CUDA tensor aliasing n elements at a device pointer."""
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Holder(), device="cuda")
+
+
+def alone(n, alpha, seed):
+    """The request computed by itself: generator inputs, one wxpy() call."""
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    return wx.wxpy(alpha, x, y)
+
+
+def request_mix(seed, count, hi):
+    ns = [1, 3, 8191, 8192, 8193, (1 << 20) + 3] + list(
+        synth.log_uniform_lengths(seed, count, 1, hi))
+    alphas = synth.uniform_pm2(seed, synth.TAG_ALPHA, len(ns))
+    seeds = [seed * 1000 + i for i in range(len(ns))]
+    return [(int(n), float(a), s) for n, a, s in zip(ns, alphas, seeds)]
+
+
+def run_requests(mode, reqs, **kw):
+    out = {}
+    with Server(budget_bytes=2 << 30, mode=mode, **kw) as sv:
+        tickets = [sv.submit(n, a, s) for (n, a, s) in reqs]
+        for t in tickets:
+            lat = sv.wait(t, 60.0)
+            assert lat > 0
+        torch.cuda.synchronize()
+        for t, (n, a, s) in zip(tickets, reqs):
+            m, px, py, pw = sv.result(t)
+            assert m == n
+            out[s] = _from_ptr(pw, n).clone()
+            sv.release(t)
+        st = sv.stats()
+        assert st["completed"] == len(reqs) and st["failed"] == 0 and st["resident_now"] == 0
+        assert st["arena_used"] == 0
+    return out, st
+
+
+def test_batched_results_equal_alone_and_oracle():
+    reqs = request_mix(31, 250, 1 << 18)
+    out, st = run_requests(SERVE_BATCHED, reqs, n_streams=2, max_batch=64)
+    assert st["batches"] < len(reqs)  # requests were coalesced
+    for (n, a, s) in reqs:
+        w_alone = alone(n, a, s)
+        assert torch.equal(out[s].view(torch.int64), w_alone.view(torch.int64)), (n, s)
+    for (n, a, s) in reqs[:40]:  # oracle on the host for a subset
+        xh = synth.uniform_pm1(s, synth.TAG_X, n)
+        yh = synth.uniform_pm1(s, synth.TAG_Y, n)
+        want = oracle.wxpy(a, xh, yh)
+        got = out[s].cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (n, s)
+
+
+def test_serial_and_batched_modes_agree():
+    reqs = request_mix(32, 80, 1 << 16)
+    a, st_a = run_requests(SERVE_BATCHED, reqs, n_streams=3, max_batch=16)
+    b, st_b = run_requests(SERVE_SERIAL, reqs, n_streams=1, max_batch=1)
+    c, st_c = run_requests(SERVE_SERIAL, reqs, n_streams=2, max_batch=32)
+    assert st_b["batches"] == len(reqs) and st_b["mean_batch"] == 1.0
+    assert st_b["launches"] == 3 * len(reqs) == st_c["launches"]
+    assert st_a["launches"] == 2 * st_a["batches"]
+    for (_, _, s) in reqs:
+        assert torch.equal(a[s].view(torch.int64), b[s].view(torch.int64))
+        assert torch.equal(a[s].view(torch.int64), c[s].view(torch.int64))
+
+
+def test_budget_slots_and_queue_limit():
+    n = 1 << 16  # 3 * 512 KiB per request
+    per = 3 * 8 * n
+    with Server(budget_bytes=2 * per, max_slots=2, n_streams=2, max_batch=8, max_queue=3) as sv:
+        with pytest.raises(wx.WxpyError) as e:
+            sv.submit(n * 3, 1.0, 1)  # can never fit the budget
+        assert e.value.status == wx.WXPY_EBUDGET
+        t = [sv.submit(n, 0.5, 100 + i) for i in range(2)]
+        for ti in t:
+            sv.wait(ti, 30.0)
+        # both slots held (results not released): new requests wait in the queue
+        q = [sv.submit(n, 0.5, 200 + i) for i in range(3)]
+        with pytest.raises(wx.WxpyError) as e:
+            sv.submit(n, 0.5, 299)  # queue of 3 is full
+        assert e.value.status == wx.WXPY_EBUSY
+        import time
+        time.sleep(0.05)
+        assert sv.poll(q[0])[0] == REQ_QUEUED
+        sv.release(t[0])
+        sv.wait(q[0], 30.0)
+        assert sv.poll(q[0])[0] == REQ_DONE
+        assert sv.poll(q[1])[0] == REQ_QUEUED
+        for ti in (t[1], q[0]):
+            sv.release(ti)
+        for ti in q[1:]:
+            sv.wait(ti, 30.0)
+            sv.release(ti)
+        st = sv.stats()
+        assert st["rejected"] == 1 and st["completed"] == 5 and st["resident_now"] == 0
+        with pytest.raises(wx.WxpyError) as e:
+            sv.poll(t[0])
+        assert e.value.status == wx.WXPY_ENOTFOUND
+
+
+def test_injected_launch_failure_fails_only_that_batch():
+    with Server(budget_bytes=256 << 20, n_streams=1, max_batch=4) as sv:
+        wx.wxpy_debug_inject_launch_error(719, 1)
+        t1 = sv.submit(5000, 1.5, 7)
+        with pytest.raises(wx.WxpyError) as e:
+            sv.wait(t1, 30.0)
+        assert e.value.status == wx.WXPY_ECUDA
+        assert sv.poll(t1)[0] == REQ_FAILED
+        sv.release(t1)
+        wx.wxpy_debug_inject_launch_error(0, 0)
+        t2 = sv.submit(5000, 1.5, 7)
+        sv.wait(t2, 30.0)
+        _, _, _, pw = sv.result(t2)
+        assert torch.equal(_from_ptr(pw, 5000).view(torch.int64),
+                           alone(5000, 1.5, 7).view(torch.int64))
+        sv.release(t2)
+        assert sv.stats()["failed"] == 1
+
+
+def test_poisson_loadgen_short():
+    with Server(budget_bytes=2 << 30, n_streams=2, max_batch=256) as sv:
+        r = sv.loadgen(rate=3000.0, duration_s=0.5, n_min=256, n_max=1 << 16, seed=5,
+                       drain_timeout_s=30.0)
+        assert r["drained"] == 1
+        assert r["completed"] == r["submitted"] > 500 and r["failed"] == 0
+        assert 0 < r["p50_s"] <= r["p99_s"] <= r["max_s"]
+        assert r["elem_per_s"] > 0
+        st = sv.stats()
+        assert st["resident_now"] == 0 and st["arena_used"] == 0
