@@ -384,11 +384,18 @@ void scheduler(wxpy_server *sv) {
             {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 const int64_t maxb = sv->cfg.max_batch;
+                // A batch holds at most its stream's share of the budget, so
+                // that the next batch can be admitted and launched on another
+                // stream while this one runs.
+                const int64_t share = sv->arena.size() / (int64_t)sv->slots.size();
+                int64_t bytes = 0;
                 size_t taken = 0;
                 for (; taken < sv->admitted.size() && (int64_t)taken < maxb &&
                        (int64_t)taken < s.cap_segs;
                      ++taken) {
                     Request &r = sv->reqs[sv->admitted[taken]];
+                    if (taken > 0 && bytes + r.bytes > share) break;
+                    bytes += r.bytes;
                     r.state = kRunning;
                     batch.push_back(&r);
                     s.tickets.push_back(sv->admitted[taken]);
