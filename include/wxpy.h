@@ -127,10 +127,15 @@ typedef struct wxpy_variant_info {
     int32_t streams;       /* 1, 2, 4, 8: the call is cut into this many
                               256-byte-aligned pieces, each on its own stream,
                               forked from and joined back into `stream` */
+    int32_t fp64_offload;  /* 0: both roundings on the FP64 pipeline; 1: the sum
+                              of every other element of a pass, 2: every sum,
+                              computed as an exactly rounded binary64 addition in
+                              the integer pipeline (same bits; the FP64 pipeline
+                              is the scarce unit on GB300) */
 } wxpy_variant_info;
 
 /* Number of variants in the space (vec_bytes x unroll x threads x grid mode x
- * cache x carveout x streams). */
+ * cache x carveout x streams x fp64_offload). */
 int wxpy_variant_count(void);
 
 /* Decodes variant `id` into *out.  WXPY_EINVAL for an id out of range. */

@@ -51,7 +51,7 @@ class VariantInfo(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int32), ("vec_bytes", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("cache", ctypes.c_int32), ("carveout", ctypes.c_int32),
-                ("streams", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("fp64_offload", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

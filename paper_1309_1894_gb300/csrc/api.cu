@@ -91,6 +91,8 @@ int index_of(const int (&arr)[N], int v) {
 }
 }  // namespace
 
+// Mixed-radix id; the offload digit is the most significant, so ids with
+// offload 0 are the ids of the space without that knob.
 bool decode_variant(int id, Variant *v) {
     if (id < 0 || id >= kVariantCount) return false;
     int r = id;
@@ -100,9 +102,10 @@ bool decode_variant(int id, Variant *v) {
     const int gr = r % 5; r /= 5;
     const int th = r % 4; r /= 4;
     const int un = r % 4; r /= 4;
-    const int vb = r;  // < 3
+    const int vb = r % 3; r /= 3;
+    const int of = r;  // < 3
     *v = Variant{kVecBytes[vb], kUnroll[un], kThreads[th], kBlocksPerSm[gr],
-                 kCache[ca], kCarveout[co], kStreams[st]};
+                 kCache[ca], kCarveout[co], kStreams[st], kOffload[of]};
     return true;
 }
 
@@ -110,9 +113,9 @@ int encode_variant(const Variant &v) {
     const int vb = index_of(kVecBytes, v.vec_bytes), un = index_of(kUnroll, v.unroll),
               th = index_of(kThreads, v.threads), gr = index_of(kBlocksPerSm, v.blocks_per_sm),
               ca = index_of(kCache, v.cache), co = index_of(kCarveout, v.carveout),
-              st = index_of(kStreams, v.streams);
-    if (vb < 0 || un < 0 || th < 0 || gr < 0 || ca < 0 || co < 0 || st < 0) return -1;
-    return ((((((vb * 4 + un) * 4 + th) * 5 + gr) * 3 + ca) * 4 + co) * 4 + st);
+              st = index_of(kStreams, v.streams), of = index_of(kOffload, v.offload);
+    if (vb < 0 || un < 0 || th < 0 || gr < 0 || ca < 0 || co < 0 || st < 0 || of < 0) return -1;
+    return (((((((of * 3 + vb) * 4 + un) * 4 + th) * 5 + gr) * 3 + ca) * 4 + co) * 4 + st);
 }
 
 void to_info(const Variant &v, int id, wxpy_variant_info *out) {
@@ -124,10 +127,12 @@ void to_info(const Variant &v, int id, wxpy_variant_info *out) {
     out->cache = v.cache;
     out->carveout = v.carveout;
     out->streams = v.streams;
+    out->fp64_offload = v.offload;
 }
 
 static Variant from_info(const wxpy_variant_info &i) {
-    return Variant{i.vec_bytes, i.unroll, i.threads, i.blocks_per_sm, i.cache, i.carveout, i.streams};
+    return Variant{i.vec_bytes, i.unroll, i.threads, i.blocks_per_sm, i.cache, i.carveout,
+                   i.streams, i.fp64_offload};
 }
 
 // ---------------------------------------------------------------- classification
@@ -261,7 +266,8 @@ int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, dou
     const int64_t head = std::min<int64_t>((vw - off) % vw, n);
     SingleArgs a{x, y, w, alpha, n, head, (n - head) / vw};
     const int u_idx = v.unroll == 1 ? 0 : v.unroll == 2 ? 1 : v.unroll == 4 ? 2 : 3;
-    const SingleEntry ent = single_entry(vw, u_idx, v.blocks_per_sm > 0 ? 1 : 0, v.cache, xy);
+    const SingleEntry ent =
+        single_entry(vw, v.offload, u_idx, v.blocks_per_sm > 0 ? 1 : 0, v.cache, xy);
     // Instances that keep many registers live per thread have a smaller launch
     // bound; the block size is capped at it.
     const int threads = std::min(v.threads, ent.max_threads);
@@ -280,11 +286,17 @@ int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, dou
 }
 }  // namespace
 
-SingleEntry single_entry(int vw, int u_idx, int gs, int cache, int xy) {
-    switch (vw) {
-        case 4: return SingleTable<4>::get(u_idx, gs, cache, xy);
-        case 2: return SingleTable<2>::get(u_idx, gs, cache, xy);
-        default: return SingleTable<1>::get(u_idx, gs, cache, xy);
+SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy) {
+    switch (vw * 3 + offload) {
+        case 4 * 3 + 0: return SingleTable<4, 0>::get(u_idx, gs, cache, xy);
+        case 4 * 3 + 1: return SingleTable<4, 1>::get(u_idx, gs, cache, xy);
+        case 4 * 3 + 2: return SingleTable<4, 2>::get(u_idx, gs, cache, xy);
+        case 2 * 3 + 0: return SingleTable<2, 0>::get(u_idx, gs, cache, xy);
+        case 2 * 3 + 1: return SingleTable<2, 1>::get(u_idx, gs, cache, xy);
+        case 2 * 3 + 2: return SingleTable<2, 2>::get(u_idx, gs, cache, xy);
+        case 1 * 3 + 1: return SingleTable<1, 1>::get(u_idx, gs, cache, xy);
+        case 1 * 3 + 2: return SingleTable<1, 2>::get(u_idx, gs, cache, xy);
+        default: return SingleTable<1, 0>::get(u_idx, gs, cache, xy);
     }
 }
 

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "gen.cuh"
@@ -29,6 +30,14 @@ __global__ void fill_uniform_kernel(double *dst, int64_t n, uint64_t key, int64_
         const double u = (double)(b >> 11) * 0x1.0p-53;
         dst[i] = __dadd_rn(lo, __dmul_rn(width, u));
     }
+}
+
+// The same values for a range (-2^s, 2^s), assembled with integer operations
+// only (see uniform_sym): no FP64 instruction per element.
+__global__ void fill_symmetric_kernel(double *dst, int64_t n, uint64_t key, int64_t start, int s) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = uniform_sym(key, start + i, s);
 }
 
 // count += number of i with bits(a[i]) != bits(b[i]).
@@ -61,8 +70,16 @@ int launch_fill_uniform(double *dst, int64_t n, uint64_t seed, uint32_t tag, int
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)dp->sm_count * 8);
     cudaError_t e = injected_launch_error();
     if (e == cudaSuccess) {
-        fill_uniform_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, stream_key(seed, tag), start,
-                                                             lo, hi - lo);
+        // (-2^s, 2^s) with a small s: the integer-only path gives the same bits.
+        int sym = -1;
+        for (int k = 0; k < 8; ++k)
+            if (lo == -std::ldexp(1.0, k) && hi == std::ldexp(1.0, k)) sym = k;
+        if (sym >= 0)
+            fill_symmetric_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, stream_key(seed, tag),
+                                                                   start, sym);
+        else
+            fill_uniform_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, stream_key(seed, tag),
+                                                                 start, lo, hi - lo);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fail_cuda(e, "fill kernel launch");

@@ -24,7 +24,9 @@ __host__ __device__ __forceinline__ uint64_t stream_key_of(uint64_t seed, uint32
 // m = 2k - 2^53 (k = b >> 11), so its binary64 encoding is assembled from m
 // with integer operations only: on GB300 the FP64 pipe is the scarce one
 // (a conversion, a multiply and an add per value would use it three times).
-__device__ __forceinline__ double uniform_pm1(uint64_t key, int64_t i) {
+// More generally, for a range of width 2^(s+1) centred on zero, the value
+// lo + width*u = m * 2^(s-53); `uniform_sym(key, i, s)` assembles that.
+__device__ __forceinline__ double uniform_sym(uint64_t key, int64_t i, int s) {
     const uint64_t b = mix64(key + (uint64_t)(i + 1) * kGolden);
     const int64_t m = (int64_t)((b >> 11) << 1) - ((int64_t)1 << 53);  // [-2^53, 2^53), even
     if (m == 0) return 0.0;
@@ -32,8 +34,12 @@ __device__ __forceinline__ double uniform_pm1(uint64_t key, int64_t i) {
     const uint64_t a = (uint64_t)(m < 0 ? -m : m);  // [2, 2^53]
     const int p = 63 - __clzll((long long)a);      // a = 1.f * 2^p, p in [1, 53]
     const uint64_t frac = (p <= 52 ? (a << (52 - p)) : (a >> (p - 52))) & ((1ull << 52) - 1);
-    const uint64_t expo = (uint64_t)(p - 53 + 1023);
+    const uint64_t expo = (uint64_t)(p - 53 + s + 1023);
     return __longlong_as_double((long long)(sign | (expo << 52) | frac));
+}
+
+__device__ __forceinline__ double uniform_pm1(uint64_t key, int64_t i) {
+    return uniform_sym(key, i, 0);
 }
 
 }  // namespace wx

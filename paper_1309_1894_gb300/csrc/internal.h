@@ -33,6 +33,7 @@ const DeviceProps *current_device(int *status);
 // ---- the variant space ----
 struct Variant {
     int vec_bytes, unroll, threads, blocks_per_sm, cache, carveout, streams;
+    int offload = 0;  // sums in the integer pipeline: 0 none, 1 half, 2 all
 };
 constexpr int kVecBytes[3] = {8, 16, 32};
 constexpr int kUnroll[4] = {1, 2, 4, 8};
@@ -41,7 +42,9 @@ constexpr int kBlocksPerSm[5] = {0, 1, 2, 4, 8};
 constexpr int kCache[3] = {0, 1, 2};
 constexpr int kCarveout[4] = {-1, 0, 50, 100};
 constexpr int kStreams[4] = {1, 2, 4, 8};
-constexpr int kVariantCount = 3 * 4 * 4 * 5 * 3 * 4 * 4;
+constexpr int kOffload[3] = {0, 1, 2};
+constexpr int kVariantsPerOffload = 3 * 4 * 4 * 5 * 3 * 4 * 4;
+constexpr int kVariantCount = kVariantsPerOffload * 3;
 
 bool decode_variant(int id, Variant *v);
 int encode_variant(const Variant &v);  // -1 if a field is out of the space
@@ -115,6 +118,6 @@ int launch_count_mismatch(const double *a, const double *b, int64_t n,
 int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s);
 
 cudaError_t launch_reference(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s);
-SingleEntry single_entry(int vw, int unroll, int gs, int cache, int xy);
+SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy);
 
 }  // namespace wx

@@ -103,8 +103,17 @@ __device__ __forceinline__ void wxpy_vec(double alpha, const double (&x)[VW],
     for (int k = 0; k < VW; ++k) w[k] = __dadd_rn(__dmul_rn(alpha, x[k]), y[k]);
 }
 
-// One pass of one thread: chunks c0, c0 + tpb, ..., c0 + (U-1)*tpb.
-template <int VW, int U, int CACHE, bool XY>
+}  // namespace wx
+
+#include "fp64_emu.cuh"
+
+namespace wx {
+
+// One pass of one thread: chunks c0, c0 + tpb, ..., c0 + (U-1)*tpb.  EMU
+// selects which sums run in the integer pipeline (fp64_emu.cuh): none, the
+// odd positions of the pass, or all; the choice depends only on the position,
+// so it is the same for every lane of a warp.
+template <int VW, int U, int CACHE, bool XY, int EMU>
 __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64_t tpb) {
     const double *xb = a.x + a.head;
     const double *yb = a.y + a.head;
@@ -119,8 +128,8 @@ __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if constexpr (XY) wxpy_vec<VW>(a.alpha, xv[u], xv[u], wv[u]);
-            else wxpy_vec<VW>(a.alpha, xv[u], yv[u], wv[u]);
+            if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], xv[u], wv[u], u * VW);
+            else wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], yv[u], wv[u], u * VW);
             st_vec<VW, CACHE>(wb + (c0 + u * tpb) * VW, wv[u]);
         }
     } else {
@@ -136,8 +145,8 @@ __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64
         for (int u = 0; u < U; ++u) {
             const int64_t c = c0 + u * tpb;
             if (c < a.nchunks) {
-                if constexpr (XY) wxpy_vec<VW>(a.alpha, xv[u], xv[u], wv[u]);
-                else wxpy_vec<VW>(a.alpha, xv[u], yv[u], wv[u]);
+                if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], xv[u], wv[u], u * VW);
+                else wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], yv[u], wv[u], u * VW);
                 st_vec<VW, CACHE>(wb + c * VW, wv[u]);
             }
         }
@@ -171,24 +180,27 @@ __device__ __forceinline__ void wxpy_edges(const SingleArgs &a, int64_t vw) {
 // of input live (two registers each) and about three 64-bit addresses per
 // unrolled vector, plus the loop state of the grid-stride form; the estimate
 // below must fit the per-thread register share 65536 / threads, so that the
-// compiler never spills to the stack.
-template <int VW, int U, int GS, bool XY>
+// compiler never spills to the stack.  The integer-pipeline sum (EMU > 0)
+// needs a handful of 64-bit temporaries more.
+template <int VW, int U, int GS, bool XY, int EMU>
 constexpr int max_threads() {
-    constexpr int regs = 2 * U * VW * (XY ? 1 : 2) + 6 * U + 20 + (GS ? 16 : 0);
+    constexpr int regs =
+        2 * U * VW * (XY ? 1 : 2) + 6 * U + 20 + (GS ? 16 : 0) + (EMU ? 24 : 0);
     return regs <= 64 ? 1024 : (regs <= 128 ? 512 : 256);
 }
 
-template <int VW, int U, int GS, int CACHE, bool XY>
-__global__ void __launch_bounds__(max_threads<VW, U, GS, XY>()) wxpy_single_kernel(const SingleArgs a) {
+template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
+__global__ void __launch_bounds__(max_threads<VW, U, GS, XY, EMU>())
+    wxpy_single_kernel(const SingleArgs a) {
     const int64_t tpb = blockDim.x;
     if constexpr (GS == 0) {
         const int64_t c0 = (int64_t)blockIdx.x * tpb * U + threadIdx.x;
-        if (c0 < a.nchunks) wxpy_pass<VW, U, CACHE, XY>(a, c0, tpb);
+        if (c0 < a.nchunks) wxpy_pass<VW, U, CACHE, XY, EMU>(a, c0, tpb);
     } else {
         const int64_t stride = (int64_t)gridDim.x * tpb * U;
         for (int64_t c0 = (int64_t)blockIdx.x * tpb * U + threadIdx.x; c0 < a.nchunks;
              c0 += stride)
-            wxpy_pass<VW, U, CACHE, XY>(a, c0, tpb);
+            wxpy_pass<VW, U, CACHE, XY, EMU>(a, c0, tpb);
     }
     wxpy_edges<CACHE, XY>(a, VW);
 }
@@ -205,20 +217,21 @@ struct SingleEntry {
     int max_threads;        // launch bound of the instance
 };
 
-template <int VW, int U, int GS, int CACHE, bool XY>
+template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
 cudaError_t launch_single(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s) {
-    wxpy_single_kernel<VW, U, GS, CACHE, XY><<<grid, tpb, 0, s>>>(a);
+    wxpy_single_kernel<VW, U, GS, CACHE, XY, EMU><<<grid, tpb, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int VW, int U, int GS, int CACHE, bool XY>
+template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
 SingleEntry make_single_entry() {
-    return SingleEntry{(const void *)&wxpy_single_kernel<VW, U, GS, CACHE, XY>,
-                       &launch_single<VW, U, GS, CACHE, XY>, max_threads<VW, U, GS, XY>()};
+    return SingleEntry{(const void *)&wxpy_single_kernel<VW, U, GS, CACHE, XY, EMU>,
+                       &launch_single<VW, U, GS, CACHE, XY, EMU>,
+                       max_threads<VW, U, GS, XY, EMU>()};
 }
 
-// Table of one VW: index ((u_idx * 2 + gs) * 3 + cache) * 2 + xy, u_idx = log2 U.
-template <int VW>
+// Table of one (VW, EMU): index ((u_idx * 2 + gs) * 3 + cache) * 2 + xy, u_idx = log2 U.
+template <int VW, int EMU>
 struct SingleTable {
     static SingleEntry get(int u_idx, int gs, int cache, int xy);
 };

@@ -211,14 +211,16 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
                                  [](const Candidate &a, const Candidate &b) { return a.us < b.us; });
     };
 
-    // Stage A: width x unroll x cache.
+    // Stage A: width x unroll x cache x FP64 offload.
     std::vector<Candidate> A;
     for (int vb : kVecBytes)
         for (int u : kUnroll) {
             if (quick && u == 1) continue;
             for (int ca : kCache) {
                 if (quick && ca == 0) continue;
-                if ((st = consider(Variant{vb, u, 256, 0, ca, -1, 1}, A)) != WXPY_OK) return st;
+                for (int of : kOffload)
+                    if ((st = consider(Variant{vb, u, 256, 0, ca, -1, 1, of}, A)) != WXPY_OK)
+                        return st;
             }
         }
     if (A.empty()) return fail(WXPY_EMISMATCH, "every candidate differed from the reference");
@@ -357,14 +359,15 @@ int cache_save(const char *path) {
         if (id < 0) continue;
         Variant v;
         decode_variant(id, &v);
-        char buf[320];
+        char buf[360];
         std::snprintf(buf, sizeof buf,
                       "%s\n    {\"key\": %d, \"bucket\": %d, \"align\": %d, \"group\": %d, "
                       "\"variant\": %d, \"vec_bytes\": %d, \"unroll\": %d, \"threads\": %d, "
-                      "\"blocks_per_sm\": %d, \"cache\": %d, \"carveout\": %d, \"streams\": %d}",
+                      "\"blocks_per_sm\": %d, \"cache\": %d, \"carveout\": %d, \"streams\": %d, "
+                      "\"fp64_offload\": %d}",
                       first ? "" : ",", k, k / 12, (k / 4) % 3 == 0 ? 32 : ((k / 4) % 3 == 1 ? 16 : 8),
                       k % 4, id, v.vec_bytes, v.unroll, v.threads, v.blocks_per_sm, v.cache,
-                      v.carveout, v.streams);
+                      v.carveout, v.streams, v.offload);
         out += buf;
         first = false;
     }

@@ -46,7 +46,10 @@ def test_strerror(lib):
 
 def test_variant_space_roundtrip(lib):
     count = wx.wxpy_variant_count()
-    assert count == 3 * 4 * 4 * 5 * 3 * 4 * 4
+    assert count == 3 * 4 * 4 * 5 * 3 * 4 * 4 * 3
+    # ids without the FP64 offload knob keep their meaning (offload is the top digit)
+    assert wx.wxpy_variant_describe(count // 3 - 1)["fp64_offload"] == 0
+    assert wx.wxpy_variant_describe(count // 3)["fp64_offload"] == 1
     seen = set()
     for vid in range(0, count, 7):
         d = wx.wxpy_variant_describe(vid)

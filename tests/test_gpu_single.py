@@ -75,7 +75,87 @@ def covering_variants():
     for s in (2, 4, 8):
         vs.append(enc(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=4, cache=1,
                       carveout=-1, streams=s))
+    for of in (1, 2):  # sums in the integer pipeline
+        for vb in (8, 16, 32):
+            for u in (1, 2, 8):
+                vs.append(enc(vec_bytes=vb, unroll=u, threads=256, blocks_per_sm=0 if u < 8 else 2,
+                              cache=1, carveout=-1, streams=1, fp64_offload=of))
     return vs
+
+
+def offload_variants():
+    enc = wx.wxpy_variant_encode
+    return [enc(vec_bytes=vb, unroll=u, threads=128, blocks_per_sm=0, cache=2, carveout=-1,
+                streams=1, fp64_offload=of)
+            for of in (1, 2) for vb in (8, 16, 32) for u in (1, 4)]
+
+
+def _special_pairs():
+    """(x, y) pairs aimed at the integer-pipeline adder: every exponent gap
+    0..70 with both signs, ties to even, cancellation, carries into the next
+    binade, overflow and underflow of the sum, zeros, subnormals, inf, NaN."""
+    import pins
+    xs, ys = [], []
+    base = [1.0, 1.0 + 2.0 ** -52, 1.5, 2.0 - 2.0 ** -52, 1.7976931348623157e308, 2.0 ** -1021,
+            3.0, 0.1]
+    for b in base:
+        for d in range(0, 71):
+            for sy in (1.0, -1.0):
+                for tweak in (1.0, 1.0 + 2.0 ** -52, 1.5, 2.0 - 2.0 ** -52):
+                    xs.append(b)
+                    ys.append(sy * np.ldexp(tweak * b, -d) if b < 1e300 else sy * np.ldexp(tweak, 1000 - d))
+    # ties: x + half an ulp of x, with x odd and even in the last place
+    for k in range(0, 1000, 37):
+        x = 1.0 + k * 2.0 ** -52
+        xs += [x, x, -x]
+        ys += [2.0 ** -53, -(2.0 ** -53), -(2.0 ** -53)]
+    sv = pins.special_values()
+    for a in sv:
+        for b in sv:
+            xs.append(a)
+            ys.append(b)
+    return np.array(xs, dtype=np.float64), np.array(ys, dtype=np.float64)
+
+
+def test_integer_pipeline_sum_is_exact():
+    """fp64_offload variants give the oracle's bits (NaN by class) on inputs
+    chosen to hit every branch of the integer-pipeline adder."""
+    import pins
+    xh, yh = _special_pairs()
+    cases = [(1.0, xh, yh)]
+    for seed in (1, 2):
+        a, x, y = pins.random_cases(synth.BASE_SEED + 300 + seed, 20000)
+        cases.append((a, x, y))
+    for alpha, x, y in cases:
+        want = oracle.wxpy(alpha, x, y)
+        xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        for vid in offload_variants():
+            w = wx.wxpy_run_variant(vid, alpha, xd, yd)
+            torch.cuda.synchronize()
+            got = w.cpu().numpy()
+            gb, wb = got.view(np.uint64), want.view(np.uint64)
+            bad = np.nonzero((gb != wb) & ~(np.isnan(got) & np.isnan(want)))[0]
+            assert bad.size == 0, (
+                f"variant {wx.wxpy_variant_describe(vid)}: {bad.size} differ, first alpha={alpha!r} "
+                f"x={x[bad[0]]!r} y={y[bad[0]]!r} got {got[bad[0]].hex()} want {want[bad[0]].hex()}")
+
+
+def test_integer_pipeline_sum_on_golden_fixture():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "special_cases.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    by_alpha = {}
+    for a, x, y, w, _ in rows:
+        by_alpha.setdefault(a, []).append((float.fromhex(x), float.fromhex(y), float.fromhex(w)))
+    for a, trip in by_alpha.items():
+        x = np.array([t[0] for t in trip])
+        y = np.array([t[1] for t in trip])
+        want = np.array([t[2] for t in trip])
+        for vid in offload_variants():
+            got = wx.wxpy_run_variant(vid, float.fromhex(a), torch.from_numpy(x).cuda(),
+                                      torch.from_numpy(y).cuda()).cpu().numpy()
+            ok = (got.view(np.uint64) == want.view(np.uint64)) | (np.isnan(got) & np.isnan(want))
+            assert ok.all(), (a, wx.wxpy_variant_describe(vid))
 
 
 @pytest.fixture(autouse=True)
@@ -86,7 +166,13 @@ def _reset_forced():
 
 
 def test_device_generator_matches_host():
-    for (lo, hi, host) in ((-1.0, 1.0, synth.uniform_pm1), (-2.0, 2.0, synth.uniform_pm2)):
+    """Integer-assembled symmetric ranges and the general FP64 path ((0, 1)) both
+    reproduce the host generator bit for bit."""
+    def u01(seed, tag, count, start=0):
+        return synth.u01(seed, tag, start, count)
+
+    for (lo, hi, host) in ((-1.0, 1.0, synth.uniform_pm1), (-2.0, 2.0, synth.uniform_pm2),
+                           (0.0, 1.0, u01)):
         d = torch.empty(100003, dtype=torch.float64, device="cuda")
         wx.wxpy_fill_uniform(d, seed=synth.BASE_SEED, tag=synth.TAG_X, lo=lo, hi=hi, start=12345)
         ok, msg = bits_equal(d, host(synth.BASE_SEED, synth.TAG_X, 100003, start=12345))
