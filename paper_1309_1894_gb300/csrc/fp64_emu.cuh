@@ -34,48 +34,75 @@
 
 namespace wx {
 
-__device__ __forceinline__ double add_rn_int(double a, double b) {
+// The hardware sum for the rare operands the integer path leaves out, on bit
+// patterns.  Kept out of line: an inlined fallback is if-converted by the
+// compiler -- issued, predicated off, for every element -- and would occupy the
+// FP64 pipeline the integer path exists to relieve; and its arguments and
+// result are integers, since the moves that set up double-typed call
+// arguments were issued for every element as well.
+static __device__ __noinline__ uint64_t add_rn_hw_bits(uint64_t ua, uint64_t ub) {
+    return (uint64_t)__double_as_longlong(
+        __dadd_rn(__longlong_as_double((long long)ua), __longlong_as_double((long long)ub)));
+}
+
+// The bit pattern of a double through an opaque register move.  Handing the
+// integer path a value the compiler still sees as a double (for instance the
+// product just computed) let it rewrite integer operations on its bits into
+// FP64-pipeline instructions.
+__device__ __forceinline__ uint64_t opaque_bits(double v) {
+    uint64_t b;
+    asm volatile("mov.b64 %0, %1;" : "=l"(b) : "d"(v));
+    return b;
+}
+
+// RN(a + b) on the bit patterns ua, ub of two binary64 values.
+__device__ __forceinline__ uint64_t add_rn_bits(uint64_t ua, uint64_t ub) {
     constexpr uint64_t kSign = 1ull << 63;
     constexpr uint64_t kAbs = kSign - 1;
     constexpr uint64_t kFrac = (1ull << 52) - 1;
     constexpr uint64_t kHidden = 1ull << 52;
-    const uint64_t ua = (uint64_t)__double_as_longlong(a);
-    const uint64_t ub = (uint64_t)__double_as_longlong(b);
     const bool a_big = (ua & kAbs) >= (ub & kAbs);
     const uint64_t hi = a_big ? ua : ub;
     const uint64_t lo = a_big ? ub : ua;
     const int ehi = (int)((hi >> 52) & 0x7FF);
     const int elo = (int)((lo >> 52) & 0x7FF);
-    if (ehi == 0x7FF || elo == 0) return __dadd_rn(a, b);  // inf/NaN, zero or subnormal
-    const int d = ehi - elo;
+    // Inf/NaN, zero or subnormal operands go to the hardware at the end.
+    bool slow = ehi == 0x7FF || elo == 0;
+    // Branch-free from here to the single fallback test: the lanes of a warp
+    // follow one path whatever the signs and exponent gaps of their operands.
+    // Every value stays an integer bit pattern until the one reinterpretation
+    // at the end: merging several double-valued return paths made the
+    // compiler issue FP64-pipeline instructions.
+    const int dd = min(ehi - elo, 63);  // a gap of 63 or more leaves only the sticky bit
     const uint64_t H = ((hi & kFrac) | kHidden) << 10;
-    uint64_t L = ((lo & kFrac) | kHidden) << 10;
-    if (d >= 64) L = 1;
-    else if (d > 0) L = (L >> d) | (uint64_t)((L << (64 - d)) != 0);
-    int e = ehi;
-    uint64_t S;
-    if (((hi ^ lo) & kSign) == 0) {
-        S = H + L;
-        if (S >> 63) {
-            S = (S >> 1) | (S & 1);
-            ++e;
-        }
-    } else {
-        S = H - L;
-        if (S == 0) return 0.0;  // exact cancellation rounds to +0
-        const int lz = __clzll((long long)S) - 1;
-        S <<= lz;
-        e -= lz;
-    }
+    const uint64_t L0 = ((lo & kFrac) | kHidden) << 10;
+    const uint64_t L = (L0 >> dd) | (uint64_t)((L0 & ((1ull << dd) - 1)) != 0);
+    // H + L, or H - L (two's complement) when the signs differ
+    const uint64_t neg = ((hi ^ lo) & kSign) ? ~0ull : 0ull;
+    uint64_t S = H + (L ^ neg) - neg;
+    const bool zero = S == 0;  // exact cancellation rounds to +0
+    // Leading one back to bit 62: one right shift after a carry (lz == 0, with
+    // the jam bit kept), or lz - 1 left shifts after a cancellation.
+    const int lz = __clzll((long long)S);
+    const uint64_t right = (S >> 1) | (S & 1);
+    const uint64_t left = S << ((lz - 1) & 63);
+    S = lz == 0 ? right : left;
+    int e = ehi + 1 - lz;
+    // Round to nearest, ties to even, at bit 10.
     uint64_t m = S >> 10;
     const uint64_t rem = S & 0x3FF;
-    if (rem > 0x200 || (rem == 0x200 && (m & 1))) ++m;
-    if (m >> 53) {
-        m >>= 1;
-        ++e;
-    }
-    if (e <= 0 || e >= 0x7FF) return __dadd_rn(a, b);  // subnormal or overflowing result
-    return __longlong_as_double((long long)((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac)));
+    m += (uint64_t)(rem > 0x200 || (rem == 0x200 && (m & 1)));
+    const int carry = (int)(m >> 53);  // rounding reached the next binade
+    m >>= carry;
+    e += carry;
+    slow = slow || (!zero && (e <= 0 || e >= 0x7FF));  // subnormal or overflowing result
+    uint64_t bits = zero ? 0ull : ((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac));
+    if (slow) bits = add_rn_hw_bits(ua, ub);
+    return bits;
+}
+
+__device__ __forceinline__ double add_rn_int(double a, double b) {
+    return __longlong_as_double((long long)add_rn_bits(opaque_bits(a), opaque_bits(b)));
 }
 
 // w = RN(RN(alpha*x) + y) for VW elements; the sum of element k runs in the
