@@ -339,6 +339,9 @@ typedef struct wxpy_batch_tune_result {
     int32_t threads;
     int32_t candidates;      /* batched launches run */
     int32_t rejected;        /* candidates whose output differed from the reference */
+    int32_t fp64_offload;    /* chosen: 0 every sum on the FP64 pipeline, 1 half of
+                                them in the integer pipeline (see wxpy_variant_info) */
+    int32_t reserved;
 } wxpy_batch_tune_result;
 
 /* For each size bucket b in [bucket_min, bucket_max] (at most 30): builds a
@@ -358,6 +361,12 @@ int wxpy_batch_tune(int bucket_min, int bucket_max, unsigned flags,
 int wxpy_batch_shape_get(int bucket, int *tile_elems, int *unroll);
 int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll);
 int wxpy_batch_shape_reset(void);
+
+/* Whole-launch knobs of the batched launch (and of the server's batches):
+ * grid = blocks_per_sm (1..32) * sm_count, and fp64_offload 0 or 1 (half of the
+ * sums in the integer pipeline, as for wxpy_variant_info).  Host only. */
+int wxpy_batch_launch_get(int *blocks_per_sm, int *fp64_offload);
+int wxpy_batch_launch_set(int blocks_per_sm, int fp64_offload);
 
 /* ---- serving: continuous batching of wxpy requests --------------------------- */
 

@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     TUNE_ALIGN16, TUNE_ALIGN8, TUNE_XY, TUNE_WALIAS, TUNE_QUICK, TUNE_RESIDENT,
     desc_table, table_to_device, BatchPlan, wxpy_batch_plan_create, wxpy_batch,
     wxpy_batch_tune, wxpy_batch_shape_get, wxpy_batch_shape_set, wxpy_batch_shape_reset,
+    wxpy_batch_launch_get, wxpy_batch_launch_set,
     ALIAS_XY, ALIAS_WX, ALIAS_WY,
     WXPY_OK, WXPY_EINVAL, WXPY_EOVERLAP, WXPY_ENOMEM, WXPY_EBUDGET, WXPY_ECUDA,
     WXPY_ETIMEOUT, WXPY_ENOTFOUND, WXPY_EBUSY, WXPY_EMISMATCH,

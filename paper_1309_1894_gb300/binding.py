@@ -113,6 +113,8 @@ SIGNATURES = {
     "wxpy_batch_shape_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_batch_shape_reset": (_INT, []),
+    "wxpy_batch_launch_get": (_INT, [ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    "wxpy_batch_launch_set": (_INT, [_INT, _INT]),
     "wxpy_batch_noalloc": (_INT, [_P, _I64, _P]),
     "wxpy_server_create": (_INT, [_P, ctypes.POINTER(_P)]),
     "wxpy_server_submit": (_INT, [_P, _I64, _D, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
@@ -330,7 +332,8 @@ class BatchTuneResult(ctypes.Structure):
                 ("us", ctypes.c_double * 64), ("gbs", ctypes.c_double * 64),
                 ("mixed_us", ctypes.c_double), ("mixed_gbs", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("fp64_offload", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def desc_table(ns, alphas, xptrs, yptrs, wptrs):
@@ -416,7 +419,7 @@ def wxpy_batch_tune(bucket_min: int, bucket_max: int, flags: int = 0) -> dict:
             "gbs": r.gbs[b]} for b in range(bucket_min, bucket_max + 1)]
     return {"buckets": per, "mixed_us": r.mixed_us, "mixed_gbs": r.mixed_gbs,
             "blocks_per_sm": r.blocks_per_sm, "threads": r.threads,
-            "candidates": r.candidates, "rejected": r.rejected}
+            "fp64_offload": r.fp64_offload, "candidates": r.candidates, "rejected": r.rejected}
 
 
 def wxpy_batch_shape_get(bucket: int) -> tuple[int, int]:
@@ -432,3 +435,13 @@ def wxpy_batch_shape_set(bucket: int, tile_elems: int, unroll: int) -> None:
 
 def wxpy_batch_shape_reset() -> None:
     check(lib().wxpy_batch_shape_reset(), "wxpy_batch_shape_reset")
+
+
+def wxpy_batch_launch_get() -> tuple[int, int]:
+    b, o = _INT(), _INT()
+    check(lib().wxpy_batch_launch_get(ctypes.byref(b), ctypes.byref(o)), "wxpy_batch_launch_get")
+    return b.value, o.value
+
+
+def wxpy_batch_launch_set(blocks_per_sm: int, fp64_offload: int) -> None:
+    check(lib().wxpy_batch_launch_set(blocks_per_sm, fp64_offload), "wxpy_batch_launch_set")

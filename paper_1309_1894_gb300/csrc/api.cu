@@ -192,7 +192,9 @@ Variant adjust_variant(const Variant &v, const CallClass &c) {
 
 Variant default_variant(const CallClass &c, int64_t n) {
     (void)n;
-    Variant v{32, 4, 256, 0, 1, -1, 1};
+    // 32-byte accesses, half the sums in the integer pipeline: the variant
+    // that streams at the HBM limit on GB300 when nothing is tuned.
+    Variant v{32, 2, 256, 0, 1, -1, 1, 1};
     return adjust_variant(v, c);
 }
 

@@ -36,6 +36,8 @@ struct SegParams {
     unsigned *status;  // bit 0: a tile exceeded its descriptor's n
 };
 
+// EMU: sums in the integer pipeline (0 none, 1 half), chosen per launch.
+template <int EMU>
 __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -48,9 +50,20 @@ __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
             if (lane == 0) atomicOr(p.status, 1u);
             continue;
         }
-        tile_wxpy(d.x + r.begin, d.y + r.begin, d.w + r.begin, d.alpha, len, lane,
-                  1 << (r.len_ul >> 30));
+        tile_wxpy<EMU>(d.x + r.begin, d.y + r.begin, d.w + r.begin, d.alpha, len, lane,
+                       1 << (r.len_ul >> 30));
     }
+}
+
+static const void *seg_kernel_fn(int offload) {
+    return offload ? (const void *)&wxpy_seg_kernel<1> : (const void *)&wxpy_seg_kernel<0>;
+}
+
+static cudaError_t seg_launch(int offload, unsigned grid, int threads, const SegParams &sp,
+                              cudaStream_t s) {
+    if (offload) wxpy_seg_kernel<1><<<grid, threads, 0, s>>>(sp);
+    else wxpy_seg_kernel<0><<<grid, threads, 0, s>>>(sp);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- shapes
@@ -63,6 +76,7 @@ BatchShape default_batch_shape() {
     BatchShape s;
     s.threads = 256;
     s.blocks_per_sm = 4;
+    s.offload = 1;
     for (int b = 0; b < kBuckets; ++b) {
         s.tile_elems[b] = b < 13 ? 0 : 8192;
         s.unroll_log2[b] = 2;
@@ -163,8 +177,7 @@ cudaError_t launch_segmented(const wxpy_desc *dev_table, const TileRec *tiles, i
     sp.tiles = tiles;
     sp.ntiles = ntiles;
     sp.status = status;
-    wxpy_seg_kernel<<<grid, shape.threads, 0, s>>>(sp);
-    return cudaGetLastError();
+    return seg_launch(shape.offload, grid, shape.threads, sp, s);
 }
 
 }  // namespace wx
@@ -254,11 +267,9 @@ int wxpy_batch_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *s
     if (plan->ntiles == 0) return WXPY_OK;
     if (!dev_table) return fail(WXPY_EINVAL, "null device table");
     cudaError_t e = injected_launch_error();
-    if (e == cudaSuccess) {
-        wxpy_seg_kernel<<<plan->grid, plan->shape.threads, 0, (cudaStream_t)stream>>>(
-            params_of(plan, dev_table));
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess)
+        e = seg_launch(plan->shape.offload, plan->grid, plan->shape.threads,
+                       params_of(plan, dev_table), (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "batch kernel launch");
     return WXPY_OK;
 }
@@ -271,7 +282,7 @@ int wxpy_batch_graph_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, v
     SegParams sp = params_of(plan, dev_table);
     void *args[] = {&sp};
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)wxpy_seg_kernel;
+    kp.func = const_cast<void *>(seg_kernel_fn(plan->shape.offload));
     kp.gridDim = dim3(plan->grid);
     kp.blockDim = dim3(plan->shape.threads);
     kp.sharedMemBytes = 0;
@@ -355,10 +366,7 @@ int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t 
             1, std::min<int64_t>((int64_t)shape.blocks_per_sm * dp->sm_count,
                                  ((int64_t)tiles.size() + wpb - 1) / wpb));
         e = injected_launch_error();
-        if (e == cudaSuccess) {
-            wxpy_seg_kernel<<<grid, shape.threads, 0, s>>>(sp);
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = seg_launch(shape.offload, grid, shape.threads, sp, s);
     }
     cudaError_t e2 = cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return fail_cuda(e, "batch launch");
@@ -504,10 +512,7 @@ int run_shape(SynthBatch &sb, const BatchShape &shape, const DeviceProps &dp, in
     // verification run on a poisoned output
     cudaError_t e = cudaMemsetAsync(sb.w.p, 0xff, (size_t)sb.slots * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sb.count.p, 0, 8, s);
-    if (e == cudaSuccess) {
-        wxpy_seg_kernel<<<grid, shape.threads, 0, s>>>(sp);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = seg_launch(shape.offload, grid, shape.threads, sp, s);
     if (e != cudaSuccess) return fail_cuda(e, "batch search launch");
     if ((st = launch_count_mismatch((const double *)sb.w.p, (const double *)sb.wref.p, sb.slots,
                                     (unsigned long long *)sb.count.p, s)))
@@ -518,7 +523,7 @@ int run_shape(SynthBatch &sb, const BatchShape &shape, const DeviceProps &dp, in
     std::vector<float> ms(reps);
     for (int r = 0; r < reps; ++r) {
         cudaEventRecord(e0, s);
-        wxpy_seg_kernel<<<grid, shape.threads, 0, s>>>(sp);
+        seg_launch(shape.offload, grid, shape.threads, sp, s);
         cudaEventRecord(e1, s);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return fail_cuda(e, "batch search timing");
         cudaEventElapsedTime(&ms[r], e0, e1);
@@ -600,26 +605,31 @@ int batch_tune_impl(int bmin, int bmax, unsigned flags, wxpy_batch_tune_result *
         SynthBatch sb;
         if ((st = make_batch(-1, bmin, bmax, &sb, s))) return st;
         double best_us = 1e30;
-        int best_bps = shape.blocks_per_sm;
-        for (int bps : {1, 2, 4, 8}) {
-            BatchShape cand = shape;
-            cand.blocks_per_sm = bps;
-            double us = 0;
-            unsigned long long bad = 0;
-            if ((st = run_shape(sb, cand, *dp, reps, s, e0, e1, &us, &bad))) return st;
-            ++candidates;
-            if (bad) {
-                ++rejected;
-                continue;
+        int best_bps = shape.blocks_per_sm, best_of = shape.offload;
+        for (int of : {0, 1})
+            for (int bps : {1, 2, 4, 8}) {
+                BatchShape cand = shape;
+                cand.blocks_per_sm = bps;
+                cand.offload = of;
+                double us = 0;
+                unsigned long long bad = 0;
+                if ((st = run_shape(sb, cand, *dp, reps, s, e0, e1, &us, &bad))) return st;
+                ++candidates;
+                if (bad) {
+                    ++rejected;
+                    continue;
+                }
+                if (us < best_us) {
+                    best_us = us;
+                    best_bps = bps;
+                    best_of = of;
+                }
             }
-            if (us < best_us) {
-                best_us = us;
-                best_bps = bps;
-            }
-        }
         shape.blocks_per_sm = best_bps;
+        shape.offload = best_of;
         if (out) {
             out->blocks_per_sm = best_bps;
+            out->fp64_offload = best_of;
             out->mixed_us = best_us;
             out->mixed_gbs = 24.0 * (double)sb.elems / (best_us * 1e-6) / 1e9;
         }

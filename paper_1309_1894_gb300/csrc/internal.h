@@ -91,6 +91,7 @@ constexpr int64_t kMaxTileElems = (1 << 30) - 32;
 struct BatchShape {
     int threads;                   // block size of the persistent kernel
     int blocks_per_sm;             // grid = blocks_per_sm * sm_count (capped by tiles)
+    int offload;                   // sums in the integer pipeline: 0 none, 1 half
     int32_t tile_elems[kBuckets];  // per size bucket of a segment; 0 = whole segment
     int8_t unroll_log2[kBuckets];  // per size bucket: log2 of the unroll
 };

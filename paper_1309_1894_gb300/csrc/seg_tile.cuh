@@ -28,6 +28,9 @@ __device__ __forceinline__ void tile_scalar(const double *x, const double *y, do
     st_vec<1, 2>(w + e, wv);
 }
 
+// EMU: which sums run in the integer pipeline (fp64_emu.cuh): 0 none, 1 the
+// odd lanes of every 32-byte vector.
+template <int EMU>
 __device__ __forceinline__ void tile_body4(const double *x, const double *y, double *w,
                                            double alpha, int64_t nch, int lane, int U) {
     const int64_t step = 32 * U;
@@ -45,7 +48,7 @@ __device__ __forceinline__ void tile_body4(const double *x, const double *y, dou
         for (int u = 0; u < kTileMaxU; ++u) {
             const int64_t c = c0 + 32 * u;
             if (u < U && c < nch) {
-                wxpy_vec<4>(alpha, xv[u], yv[u], wv[u]);
+                wxpy_vec_emu<4, EMU>(alpha, xv[u], yv[u], wv[u], 0);
                 st_vec<4, 2>(w + c * 4, wv[u]);
             }
         }
@@ -53,6 +56,7 @@ __device__ __forceinline__ void tile_body4(const double *x, const double *y, dou
 }
 
 // The whole tile [x, x+len) by the calling warp (lane = thread index mod 32).
+template <int EMU>
 __device__ __forceinline__ void tile_wxpy(const double *x, const double *y, double *w,
                                           double alpha, int64_t len, int lane, int U) {
     const uintptr_t ax = (uintptr_t)x, ay = (uintptr_t)y, aw = (uintptr_t)w;
@@ -63,7 +67,7 @@ __device__ __forceinline__ void tile_wxpy(const double *x, const double *y, doub
         if (lane < head) tile_scalar(x, y, w, alpha, lane);
         if (lane >= 4 && body_end + (lane - 4) < len)
             tile_scalar(x, y, w, alpha, body_end + (lane - 4));
-        tile_body4(x + head, y + head, w + head, alpha, nch, lane, U);
+        tile_body4<EMU>(x + head, y + head, w + head, alpha, nch, lane, U);
     } else {
         for (int64_t e = lane; e < len; e += 32) tile_scalar(x, y, w, alpha, e);
     }

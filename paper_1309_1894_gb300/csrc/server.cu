@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
 }
 
 // w = RN(RN(alpha*x) + y) for every request of a batch, tile by tile.
+template <int EMU>
 __global__ void __launch_bounds__(256, 2) serve_wxpy_kernel(const wxpy_desc *table,
                                                             const ServePlan *plan, int64_t count,
                                                             int64_t ntiles) {
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(256, 2) serve_wxpy_kernel(const wxpy_desc *tab
         const ServePlan sp = plan[s];
         const int64_t begin = (t - sp.first_tile) * sp.tile_len;
         const int64_t len = min(sp.tile_len, d.n - begin);
-        if (len > 0) tile_wxpy(d.x + begin, d.y + begin, d.w + begin, d.alpha, len, lane, 1 << sp.ulog);
+        if (len > 0)
+            tile_wxpy<EMU>(d.x + begin, d.y + begin, d.w + begin, d.alpha, len, lane, 1 << sp.ulog);
     }
 }
 
@@ -327,7 +329,10 @@ cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> 
     serve_fill_kernel<<<fill_grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
                                                        ntiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    serve_wxpy_kernel<<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
+    if (shape.offload)
+        serve_wxpy_kernel<1><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
+    else
+        serve_wxpy_kernel<0><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sv->launches += 2;
     return cudaEventRecord(s.done, s.stream);

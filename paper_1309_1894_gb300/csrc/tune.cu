@@ -340,9 +340,11 @@ int cache_save(const char *path) {
     std::string out = "{\n  \"format\": \"wxpy-tune-1\",\n  \"device\": \"" + device_key(*dp) + "\",";
     {
         const BatchShape bs = current_batch_shape();
-        char buf[160];
-        std::snprintf(buf, sizeof buf, "\n  \"batch_launch\": {\"threads\": %d, \"blocks_per_sm\": %d},",
-                      bs.threads, bs.blocks_per_sm);
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "\n  \"batch_launch\": {\"threads\": %d, \"blocks_per_sm\": %d, "
+                      "\"fp64_offload\": %d},",
+                      bs.threads, bs.blocks_per_sm, bs.offload);
         out += buf;
         out += "\n  \"batch\": [";
         for (int b = 0; b < kBuckets; ++b) {
@@ -442,6 +444,11 @@ int cache_load(const char *path, const char *expect_device) {
                 return fail(WXPY_EINVAL, "%s: malformed batch_launch", path);
             bs.threads = (int)th;
             bs.blocks_per_sm = (int)bps;
+            long long of = -1;  // optional (files written before the knob existed)
+            if (find_int(s, lpos, lend, "fp64_offload", &of)) {
+                if (of < 0 || of > 1) return fail(WXPY_EINVAL, "%s: malformed batch_launch", path);
+                bs.offload = (int)of;
+            }
         }
     }
     for (auto &kv : entries) g_tuned[kv.first].store(kv.second);

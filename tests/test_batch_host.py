@@ -81,3 +81,16 @@ def test_cache_file_with_batch_shapes(tmp_path):
     assert wx.wxpy_tune_get(100) == -1
     wx.wxpy_batch_shape_reset()
     wx.wxpy_tune_clear()
+
+
+def test_batch_launch_knobs():
+    wx.wxpy_batch_shape_reset()
+    bps, of = wx.wxpy_batch_launch_get()
+    assert 1 <= bps <= 32 and of in (0, 1)
+    wx.wxpy_batch_launch_set(8, 0)
+    assert wx.wxpy_batch_launch_get() == (8, 0)
+    for bad in ((0, 0), (33, 0), (4, 2), (4, -1)):
+        with pytest.raises(wx.WxpyError):
+            wx.wxpy_batch_launch_set(*bad)
+    wx.wxpy_batch_shape_reset()
+    assert wx.wxpy_batch_launch_get() == (bps, of)

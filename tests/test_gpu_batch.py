@@ -98,8 +98,10 @@ def _shapes():
     wx.wxpy_batch_shape_reset()
 
 
+@pytest.mark.parametrize("offload", [0, 1])
 @pytest.mark.parametrize("mode", ["launch", "graph", "oneshot"])
-def test_batch_matches_oracle(mode):
+def test_batch_matches_oracle(mode, offload):
+    wx.wxpy_batch_launch_set(4, offload)
     ns = edge_lengths() + list(synth.log_uniform_lengths(synth.BASE_SEED + 11, 300, 1, 1 << 17))
     b = Batch(ns, synth.BASE_SEED + 11)
     t = b.table()
