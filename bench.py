@@ -72,7 +72,7 @@ def kernel_source_hash() -> str:
     """Hash of the single-call kernel sources; a profile summary records it, so
     that a stale ncu traffic figure is never reported against a changed kernel."""
     h = hashlib.sha256()
-    for name in ("single_kernel.cuh", "kernels_vw4.cu"):
+    for name in ("single_kernel.cuh", "fp64_emu.cuh"):
         with open(os.path.join(ROOT, "paper_1309_1894_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -395,6 +395,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras:
         result["sweep"] = measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak)
+        result["fp64_offload"] = measure_offload(wx, lib, torch, x, y, w, alpha, sh, stream,
+                                                 peak, variants[1 << DOMINANT_K][0])
     result["e2e"] = measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist)
     del x, y, w
     torch.cuda.empty_cache()
@@ -488,9 +490,38 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
     return out
 
 
+def measure_offload(wx, lib, torch, x, y, w, alpha, sh, stream, peak, tuned, reps=20):
+    """The tuned n = 2^28 variant with each FP64-offload setting: every sum on
+    the FP64 pipeline (0), half (1) or all (2) in the integer pipeline.  On
+    GB300 the FP64 pipeline caps two FP64 instructions per element near
+    6.2 TB/s; moving half the sums to the integer pipeline lifts that ceiling."""
+    n = 1 << DOMINANT_K
+    out = []
+    for of in (0, 1, 2):
+        fields = {k: v for k, v in tuned.items() if k != "id"}
+        fields["fp64_offload"] = of
+        vid = wx.wxpy_variant_encode(**fields)
+        args = (vid, n, alpha, x.data_ptr(), y.data_ptr(), w.data_ptr(), sh)
+        for _ in range(3):
+            wx.check(lib.wxpy_run_variant(*args), "wxpy_run_variant")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lib.wxpy_run_variant(*args)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = BYTES_PER_ELEM * n / (ms / 1e3) / 1e9
+        out.append({"fp64_offload": of, "variant": vid, "gbs": gbs, "frac_of_peak": gbs / peak})
+    return {"n": n, "reps": reps, "results": out}
+
+
 def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
-    """The sweep end to end from pinned host memory: per call, copy x and y in,
-    run wxpy, copy w out, all on one stream; bytes counted from the copies."""
+    """The sweep end to end from pinned host memory through the C ABI call
+    wxpy_host(): per call the library copies x and y in, runs the tuned kernel
+    and copies w out, chunk by chunk, overlapped on its internal streams, all
+    inside the timed region; bytes counted from the copies."""
     nmax = max(n for n, _ in calls)
     steps = max(1, args.e2e_steps)
     hx = torch.empty(nmax + 8, dtype=torch.float64, pin_memory=True)
@@ -498,20 +529,13 @@ def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
     hw = torch.empty_like(hx, pin_memory=True)
     hx.uniform_(-1, 1)
     hy.uniform_(-1, 1)
-    dx = torch.empty(nmax + 8, dtype=torch.float64, device=dev)
-    dy = torch.empty_like(dx)
-    dw = torch.empty_like(dx)
     h2d = sum(16 * n for n, _ in calls)
     d2h = sum(8 * n for n, _ in calls)
+    px, py, pw = hx.data_ptr(), hy.data_ptr(), hw.data_ptr()
 
     def step():
         for (n, o) in calls:
-            dx[o:o + n].copy_(hx[o:o + n], non_blocking=True)
-            dy[o:o + n].copy_(hy[o:o + n], non_blocking=True)
-            rc = lib.wxpy(n, alpha, dx.data_ptr() + 8 * o, dy.data_ptr() + 8 * o,
-                          dw.data_ptr() + 8 * o, sh)
-            wx.check(rc, "wxpy")
-            hw[o:o + n].copy_(dw[o:o + n], non_blocking=True)
+            wx.check(lib.wxpy_host(n, alpha, px + 8 * o, py + 8 * o, pw + 8 * o, sh), "wxpy_host")
 
     step()
     torch.cuda.synchronize()
@@ -525,11 +549,12 @@ def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
     torch.cuda.synchronize()
     ms = max_over_ranks(dist, e0.elapsed_time(e1))
     total = sum_over_ranks(dist, sum(BYTES_PER_ELEM * n for n, _ in calls) * steps)
-    del hx, hy, hw, dx, dy, dw
+    del hx, hy, hw
     return {"value": total / (ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps,
-            "how": "per call: pinned host x, y -> device, wxpy(), device w -> pinned host, "
-                   "one stream, copies inside the timed region"}
+            "how": "per call: wxpy_host() on pinned host x, y, w -- chunked copies in, tuned "
+                   "kernel, copies out, overlapped on 3 internal streams; copies inside the "
+                   "timed region"}
 
 
 def batch_layout(ns):
@@ -654,8 +679,8 @@ def measure_streams(wx, lib, torch, dev, sh, stream, peak, reps=50, warm=10):
     wx.wxpy_fill_uniform(y, 1, 2)
     out = []
     for s in (1, 2, 4, 8):
-        vid = wx.wxpy_variant_encode(vec_bytes=32, unroll=4, threads=256, blocks_per_sm=0,
-                                     cache=1, carveout=-1, streams=s)
+        vid = wx.wxpy_variant_encode(vec_bytes=32, unroll=2, threads=256, blocks_per_sm=0,
+                                     cache=1, carveout=-1, streams=s, fp64_offload=1)
         args = (vid, n, 0.5, x.data_ptr(), y.data_ptr(), w.data_ptr(), sh)
         for _ in range(warm):
             wx.check(lib.wxpy_run_variant(*args), "wxpy_run_variant")

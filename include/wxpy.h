@@ -168,6 +168,25 @@ int wxpy_lookup(int64_t n, const double *x, const double *y, const double *w,
 int wxpy(int64_t n, double alpha, const double *x, const double *y, double *w,
          void *stream);
 
+/* w = RN(RN(alpha*x[i]) + y[i]) for vectors in HOST memory (Sec. 3, Fig. 1
+ * vecwxpy), the same bits as wxpy().  The library copies x and y to device
+ * staging buffers in chunks, runs wxpy() on each chunk and copies w back,
+ * with the copies in, the kernel and the copies out of different chunks
+ * overlapping on internal streams that fork from and join back into
+ * `stream`.  Asynchronous on `stream`: the host buffers must stay valid, and
+ * hw unread, until the stream reaches the end of the call.  Host buffers
+ * should be pinned (cudaHostAlloc / cudaHostRegister); pageable memory works
+ * but the copies then do not overlap.  The staging buffers (3 x slots x
+ * chunk elements) are allocated on a device's first call and kept; calls on
+ * one device are serialised by a mutex while they enqueue.  Validation and
+ * aliasing rules are those of wxpy().  Errors: as wxpy(), plus WXPY_ENOMEM. */
+int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, double *hw,
+              void *stream);
+
+/* Chunk length (a multiple of 32 in [4096, 2^30]; default 2^22) and number of
+ * pipeline slots (1..8; default 3) of later wxpy_host() calls. */
+int wxpy_host_config(int64_t chunk_elems, int slots);
+
 /* The same operation with variant `id` (the tuner's and the tests' entry).
  * The variant is adjusted to the call's class as described at wxpy_lookup. */
 int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,

@@ -113,6 +113,8 @@ SIGNATURES = {
     "wxpy_batch_shape_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_batch_shape_reset": (_INT, []),
+    "wxpy_host": (_INT, [_I64, _D, _P, _P, _P, _P]),
+    "wxpy_host_config": (_INT, [_I64, _INT]),
     "wxpy_batch_launch_get": (_INT, [ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_launch_set": (_INT, [_INT, _INT]),
     "wxpy_batch_noalloc": (_INT, [_P, _I64, _P]),
@@ -257,6 +259,34 @@ def wxpy(alpha: float, x, y, w=None, stream=None):
     n, a, px, py, pw, w = _prepare(alpha, x, y, w)
     check(lib().wxpy(n, a, px, py, pw, _stream_handle(stream)), "wxpy")
     return w
+
+
+def _host_vec(t, name: str):
+    """(n, host pointer) of a contiguous 1-D float64 CPU tensor or numpy array."""
+    import numpy as np
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or t.ndim != 1 or not t.flags.c_contiguous:
+            raise ValueError(f"{name} must be a contiguous 1-D float64 array")
+        return t.shape[0], t.ctypes.data
+    if t.dtype.__str__() != "torch.float64" or t.is_cuda or t.dim() != 1 or (
+            t.numel() > 1 and t.stride(0) != 1):
+        raise ValueError(f"{name} must be a contiguous 1-D float64 CPU tensor")
+    return t.numel(), t.data_ptr()
+
+
+def wxpy_host(alpha: float, x, y, w, stream=None):
+    """w = alpha*x + y on host vectors (pinned for overlap), asynchronous on ``stream``."""
+    n, px = _host_vec(x, "x")
+    ny, py = _host_vec(y, "y")
+    nw, pw = _host_vec(w, "w")
+    if not (n == ny == nw):
+        raise ValueError(f"length mismatch: x {n}, y {ny}, w {nw}")
+    check(lib().wxpy_host(n, float(alpha), px, py, pw, _stream_handle(stream)), "wxpy_host")
+    return w
+
+
+def wxpy_host_config(chunk_elems: int, slots: int) -> None:
+    check(lib().wxpy_host_config(chunk_elems, slots), "wxpy_host_config")
 
 
 def wxpy_run_variant(vid: int, alpha: float, x, y, w=None, stream=None):

@@ -1,0 +1,145 @@
+// host.cu -- VecWXPY on vectors that live in host memory.
+//
+// wxpy_host() streams the vectors through device staging buffers in chunks,
+// on `slots` internal streams: while chunk i is being computed (the tuned
+// wxpy() kernel), chunk i+1's x and y are copied in and chunk i-1's w is
+// copied out, so the host-to-device and device-to-host directions of the link
+// and the kernel all overlap.  Chunk c uses slot c mod slots; stream order on
+// that slot's stream keeps a buffer from being refilled before its previous
+// contents have been copied out.  The result is w = RN(RN(alpha*x) + y) (paper
+// Sec. 3, Fig. 1 vecwxpy) element by element, the same bits as wxpy().
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+
+namespace wx {
+namespace {
+
+constexpr int kMaxDev = 64;
+constexpr int kMaxSlots = 8;
+
+struct HostPipe {
+    std::mutex mu;
+    int64_t chunk = 0;  // elements per chunk the buffers were sized for
+    int slots = 0;
+    double *buf[kMaxSlots][3] = {};
+    cudaStream_t streams[kMaxSlots] = {};
+    cudaEvent_t fork = nullptr, join[kMaxSlots] = {};
+};
+HostPipe g_pipe[kMaxDev];
+
+std::mutex g_cfg_mu;
+int64_t g_chunk = (int64_t)1 << 22;  // 32 MiB per vector per chunk
+int g_slots = 3;
+
+void release(HostPipe &p) {
+    for (int k = 0; k < p.slots; ++k) {
+        if (p.streams[k]) cudaStreamSynchronize(p.streams[k]);
+        for (int v = 0; v < 3; ++v)
+            if (p.buf[k][v]) cudaFree(p.buf[k][v]);
+        if (p.streams[k]) cudaStreamDestroy(p.streams[k]);
+        if (p.join[k]) cudaEventDestroy(p.join[k]);
+        p.buf[k][0] = p.buf[k][1] = p.buf[k][2] = nullptr;
+        p.streams[k] = nullptr;
+        p.join[k] = nullptr;
+    }
+    if (p.fork) cudaEventDestroy(p.fork);
+    p.fork = nullptr;
+    p.slots = 0;
+    p.chunk = 0;
+}
+
+int ensure(HostPipe &p, int64_t chunk, int slots) {
+    if (p.chunk == chunk && p.slots == slots) return WXPY_OK;
+    release(p);
+    cudaError_t e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+    for (int k = 0; k < slots && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&p.streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming);
+        for (int v = 0; v < 3 && e == cudaSuccess; ++v)
+            e = cudaMalloc(&p.buf[k][v], (size_t)chunk * 8 + 256);
+    }
+    p.slots = slots;  // so that release() frees whatever was made
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release(p);
+        return fail(WXPY_ENOMEM, "host pipeline staging of %d x 3 x %lld elements", slots,
+                    (long long)chunk);
+    }
+    p.chunk = chunk;
+    return WXPY_OK;
+}
+
+}  // namespace
+}  // namespace wx
+
+using namespace wx;
+
+extern "C" {
+
+int wxpy_host_config(int64_t chunk_elems, int slots) {
+    if (chunk_elems < 4096 || chunk_elems > ((int64_t)1 << 30) || (chunk_elems % 32) != 0 ||
+        slots < 1 || slots > kMaxSlots)
+        return fail(WXPY_EINVAL, "chunk must be a multiple of 32 in [4096, 2^30], slots 1..%d",
+                    kMaxSlots);
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_chunk = chunk_elems;
+    g_slots = slots;
+    return WXPY_OK;
+}
+
+int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, double *hw,
+              void *stream) {
+    CallClass c;
+    int st = classify(n, hx, hy, hw, &c);  // same validation as on device pointers
+    if (st != WXPY_OK || n == 0) return st;
+    const DeviceProps *dp = current_device(&st);
+    if (!dp) return st;
+    int64_t chunk;
+    int slots;
+    {
+        std::lock_guard<std::mutex> lk(g_cfg_mu);
+        chunk = g_chunk;
+        slots = g_slots;
+    }
+    HostPipe &p = g_pipe[dp->device];
+    std::lock_guard<std::mutex> lk(p.mu);
+    if ((st = ensure(p, chunk, slots)) != WXPY_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool same_xy = hx == hy;
+    cudaError_t e = cudaEventRecord(p.fork, s);
+    for (int k = 0; k < slots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p.streams[k], p.fork, 0);
+    if (e != cudaSuccess) return fail_cuda(e, "host pipeline fork");
+    int result = WXPY_OK;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    for (int64_t i = 0; i < nchunks && result == WXPY_OK; ++i) {
+        const int k = (int)(i % slots);
+        const int64_t off = i * chunk, len = std::min<int64_t>(chunk, n - off);
+        const size_t bytes = (size_t)len * 8;
+        cudaStream_t sk = p.streams[k];
+        double *dx = p.buf[k][0], *dy = same_xy ? p.buf[k][0] : p.buf[k][1], *dw = p.buf[k][2];
+        e = cudaMemcpyAsync(dx, hx + off, bytes, cudaMemcpyHostToDevice, sk);
+        if (e == cudaSuccess && !same_xy)
+            e = cudaMemcpyAsync(dy, hy + off, bytes, cudaMemcpyHostToDevice, sk);
+        if (e != cudaSuccess) {
+            result = fail_cuda(e, "host pipeline copy in");
+            break;
+        }
+        result = wxpy(len, alpha, dx, dy, dw, sk);
+        if (result != WXPY_OK) break;
+        e = cudaMemcpyAsync(hw + off, dw, bytes, cudaMemcpyDeviceToHost, sk);
+        if (e != cudaSuccess) result = fail_cuda(e, "host pipeline copy out");
+    }
+    // Join every slot back into the caller's stream, even after an error.
+    for (int k = 0; k < slots; ++k) {
+        e = cudaEventRecord(p.join[k], p.streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p.join[k], 0);
+        if (e != cudaSuccess && result == WXPY_OK) result = fail_cuda(e, "host pipeline join");
+    }
+    return result;
+}
+
+}  // extern "C"
