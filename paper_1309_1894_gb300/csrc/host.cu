@@ -1,13 +1,15 @@
 // host.cu -- VecWXPY on vectors that live in host memory.
 //
-// wxpy_host() streams the vectors through device staging buffers in chunks,
-// on `slots` internal streams: while chunk i is being computed (the tuned
-// wxpy() kernel), chunk i+1's x and y are copied in and chunk i-1's w is
-// copied out, so the host-to-device and device-to-host directions of the link
-// and the kernel all overlap.  Chunk c uses slot c mod slots; stream order on
-// that slot's stream keeps a buffer from being refilled before its previous
-// contents have been copied out.  The result is w = RN(RN(alpha*x) + y) (paper
-// Sec. 3, Fig. 1 vecwxpy) element by element, the same bits as wxpy().
+// wxpy_host() streams the vectors through device staging buffers in chunks.
+// Three internal streams carry, in chunk order, all copies in (host to
+// device), all kernels (the tuned wxpy()) and all copies out: while chunk i is
+// computed, chunk i+1 is copied in and chunk i-1 is copied out, so both link
+// directions and the kernel overlap, and a copy out that waits for its kernel
+// never stands in front of the next copy in.  Chunk c uses staging slot
+// c mod slots; per-slot events order copy in -> kernel -> copy out, and keep a
+// slot from being refilled before its previous contents have been copied out.
+// The result is w = RN(RN(alpha*x) + y) (paper Sec. 3, Fig. 1 vecwxpy)
+// element by element, the same bits as wxpy().
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,13 +23,16 @@ namespace {
 constexpr int kMaxDev = 64;
 constexpr int kMaxSlots = 8;
 
+enum { kIn = 0, kComp = 1, kOut = 2 };
+
 struct HostPipe {
     std::mutex mu;
     int64_t chunk = 0;  // elements per chunk the buffers were sized for
     int slots = 0;
     double *buf[kMaxSlots][3] = {};
-    cudaStream_t streams[kMaxSlots] = {};
-    cudaEvent_t fork = nullptr, join[kMaxSlots] = {};
+    cudaStream_t streams[3] = {};             // copies in, kernels, copies out
+    cudaEvent_t done[kMaxSlots][3] = {};      // per slot: copied in, computed, copied out
+    cudaEvent_t fork = nullptr, join[3] = {};
 };
 HostPipe g_pipe[kMaxDev];
 
@@ -36,15 +41,20 @@ int64_t g_chunk = (int64_t)1 << 22;  // 32 MiB per vector per chunk
 int g_slots = 3;
 
 void release(HostPipe &p) {
-    for (int k = 0; k < p.slots; ++k) {
-        if (p.streams[k]) cudaStreamSynchronize(p.streams[k]);
-        for (int v = 0; v < 3; ++v)
+    for (auto &s : p.streams)
+        if (s) cudaStreamSynchronize(s);
+    for (int k = 0; k < kMaxSlots; ++k)
+        for (int v = 0; v < 3; ++v) {
             if (p.buf[k][v]) cudaFree(p.buf[k][v]);
-        if (p.streams[k]) cudaStreamDestroy(p.streams[k]);
-        if (p.join[k]) cudaEventDestroy(p.join[k]);
-        p.buf[k][0] = p.buf[k][1] = p.buf[k][2] = nullptr;
-        p.streams[k] = nullptr;
-        p.join[k] = nullptr;
+            if (p.done[k][v]) cudaEventDestroy(p.done[k][v]);
+            p.buf[k][v] = nullptr;
+            p.done[k][v] = nullptr;
+        }
+    for (int j = 0; j < 3; ++j) {
+        if (p.streams[j]) cudaStreamDestroy(p.streams[j]);
+        if (p.join[j]) cudaEventDestroy(p.join[j]);
+        p.streams[j] = nullptr;
+        p.join[j] = nullptr;
     }
     if (p.fork) cudaEventDestroy(p.fork);
     p.fork = nullptr;
@@ -56,12 +66,15 @@ int ensure(HostPipe &p, int64_t chunk, int slots) {
     if (p.chunk == chunk && p.slots == slots) return WXPY_OK;
     release(p);
     cudaError_t e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
-    for (int k = 0; k < slots && e == cudaSuccess; ++k) {
-        e = cudaStreamCreateWithFlags(&p.streams[k], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming);
-        for (int v = 0; v < 3 && e == cudaSuccess; ++v)
-            e = cudaMalloc(&p.buf[k][v], (size_t)chunk * 8 + 256);
+    for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+        e = cudaStreamCreateWithFlags(&p.streams[j], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.join[j], cudaEventDisableTiming);
     }
+    for (int k = 0; k < slots && e == cudaSuccess; ++k)
+        for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+            e = cudaMalloc(&p.buf[k][v], (size_t)chunk * 8 + 256);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done[k][v], cudaEventDisableTiming);
+        }
     p.slots = slots;  // so that release() frees whatever was made
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -109,9 +122,10 @@ int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, doubl
     std::lock_guard<std::mutex> lk(p.mu);
     if ((st = ensure(p, chunk, slots)) != WXPY_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t s_in = p.streams[kIn], s_comp = p.streams[kComp], s_out = p.streams[kOut];
     const bool same_xy = hx == hy;
     cudaError_t e = cudaEventRecord(p.fork, s);
-    for (int k = 0; k < slots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p.streams[k], p.fork, 0);
+    for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(p.streams[j], p.fork, 0);
     if (e != cudaSuccess) return fail_cuda(e, "host pipeline fork");
     int result = WXPY_OK;
     const int64_t nchunks = (n + chunk - 1) / chunk;
@@ -119,24 +133,34 @@ int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, doubl
         const int k = (int)(i % slots);
         const int64_t off = i * chunk, len = std::min<int64_t>(chunk, n - off);
         const size_t bytes = (size_t)len * 8;
-        cudaStream_t sk = p.streams[k];
         double *dx = p.buf[k][0], *dy = same_xy ? p.buf[k][0] : p.buf[k][1], *dw = p.buf[k][2];
-        e = cudaMemcpyAsync(dx, hx + off, bytes, cudaMemcpyHostToDevice, sk);
+        // copy in, once the slot's previous contents -- of this call or of an
+        // earlier one, on whatever stream -- have been copied out (a wait on an
+        // event never recorded returns at once)
+        e = cudaStreamWaitEvent(s_in, p.done[k][kOut], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dx, hx + off, bytes, cudaMemcpyHostToDevice, s_in);
         if (e == cudaSuccess && !same_xy)
-            e = cudaMemcpyAsync(dy, hy + off, bytes, cudaMemcpyHostToDevice, sk);
+            e = cudaMemcpyAsync(dy, hy + off, bytes, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(p.done[k][kIn], s_in);
+        // compute
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, p.done[k][kIn], 0);
         if (e != cudaSuccess) {
             result = fail_cuda(e, "host pipeline copy in");
             break;
         }
-        result = wxpy(len, alpha, dx, dy, dw, sk);
+        result = wxpy(len, alpha, dx, dy, dw, s_comp);
         if (result != WXPY_OK) break;
-        e = cudaMemcpyAsync(hw + off, dw, bytes, cudaMemcpyDeviceToHost, sk);
+        e = cudaEventRecord(p.done[k][kComp], s_comp);
+        // copy out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, p.done[k][kComp], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw + off, dw, bytes, cudaMemcpyDeviceToHost, s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(p.done[k][kOut], s_out);
         if (e != cudaSuccess) result = fail_cuda(e, "host pipeline copy out");
     }
-    // Join every slot back into the caller's stream, even after an error.
-    for (int k = 0; k < slots; ++k) {
-        e = cudaEventRecord(p.join[k], p.streams[k]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p.join[k], 0);
+    // Join the three streams back into the caller's stream, even after an error.
+    for (int j = 0; j < 3; ++j) {
+        e = cudaEventRecord(p.join[j], p.streams[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p.join[j], 0);
         if (e != cudaSuccess && result == WXPY_OK) result = fail_cuda(e, "host pipeline join");
     }
     return result;
