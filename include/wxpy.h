@@ -183,9 +183,13 @@ int wxpy(int64_t n, double alpha, const double *x, const double *y, double *w,
 int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, double *hw,
               void *stream);
 
-/* Chunk length (a multiple of 32 in [4096, 2^30]; default 2^22) and number of
- * pipeline slots (1..8; default 3) of later wxpy_host() calls. */
-int wxpy_host_config(int64_t chunk_elems, int slots);
+/* Chunk length (a multiple of 32 in [4096, 2^30]; default 2^22), number of
+ * pipeline slots (1..8; default 3) and strategy of later wxpy_host() calls.
+ * direct = 1: when all three buffers are mapped pinned memory (the runtime
+ * gives them device addresses), the kernel reads x, y and writes w across the
+ * host link itself -- no staging, both link directions at once; otherwise
+ * (direct = 0, or unmapped memory) the staged pipeline above. */
+int wxpy_host_config(int64_t chunk_elems, int slots, int direct);
 
 /* The same operation with variant `id` (the tuner's and the tests' entry).
  * The variant is adjusted to the call's class as described at wxpy_lookup. */

@@ -114,7 +114,7 @@ SIGNATURES = {
     "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_batch_shape_reset": (_INT, []),
     "wxpy_host": (_INT, [_I64, _D, _P, _P, _P, _P]),
-    "wxpy_host_config": (_INT, [_I64, _INT]),
+    "wxpy_host_config": (_INT, [_I64, _INT, _INT]),
     "wxpy_batch_launch_get": (_INT, [ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_launch_set": (_INT, [_INT, _INT]),
     "wxpy_batch_noalloc": (_INT, [_P, _I64, _P]),
@@ -285,8 +285,8 @@ def wxpy_host(alpha: float, x, y, w, stream=None):
     return w
 
 
-def wxpy_host_config(chunk_elems: int, slots: int) -> None:
-    check(lib().wxpy_host_config(chunk_elems, slots), "wxpy_host_config")
+def wxpy_host_config(chunk_elems: int = 1 << 22, slots: int = 3, direct: bool = False) -> None:
+    check(lib().wxpy_host_config(chunk_elems, slots, int(direct)), "wxpy_host_config")
 
 
 def wxpy_run_variant(vid: int, alpha: float, x, y, w=None, stream=None):

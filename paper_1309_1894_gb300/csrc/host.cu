@@ -39,6 +39,17 @@ HostPipe g_pipe[kMaxDev];
 std::mutex g_cfg_mu;
 int64_t g_chunk = (int64_t)1 << 22;  // 32 MiB per vector per chunk
 int g_slots = 3;
+int g_direct = 0;
+
+// Device addresses of mapped (pinned) host memory, or false when the runtime
+// does not map the pointer.
+bool mapped(const void *h, void **d) {
+    if (cudaHostGetDevicePointer(d, const_cast<void *>(h), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
 
 void release(HostPipe &p) {
     for (auto &s : p.streams)
@@ -93,14 +104,16 @@ using namespace wx;
 
 extern "C" {
 
-int wxpy_host_config(int64_t chunk_elems, int slots) {
+int wxpy_host_config(int64_t chunk_elems, int slots, int direct) {
     if (chunk_elems < 4096 || chunk_elems > ((int64_t)1 << 30) || (chunk_elems % 32) != 0 ||
-        slots < 1 || slots > kMaxSlots)
-        return fail(WXPY_EINVAL, "chunk must be a multiple of 32 in [4096, 2^30], slots 1..%d",
+        slots < 1 || slots > kMaxSlots || direct < 0 || direct > 1)
+        return fail(WXPY_EINVAL,
+                    "chunk must be a multiple of 32 in [4096, 2^30], slots 1..%d, direct 0 or 1",
                     kMaxSlots);
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     g_chunk = chunk_elems;
     g_slots = slots;
+    g_direct = direct;
     return WXPY_OK;
 }
 
@@ -112,11 +125,19 @@ int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, doubl
     const DeviceProps *dp = current_device(&st);
     if (!dp) return st;
     int64_t chunk;
-    int slots;
+    int slots, direct;
     {
         std::lock_guard<std::mutex> lk(g_cfg_mu);
         chunk = g_chunk;
         slots = g_slots;
+        direct = g_direct;
+    }
+    if (direct) {
+        // Zero-copy: the kernel reads x, y and writes w across the link itself,
+        // both directions at once, when all three are mapped pinned memory.
+        void *dx = nullptr, *dy = nullptr, *dw = nullptr;
+        if (mapped(hx, &dx) && mapped(hy, &dy) && mapped(hw, &dw))
+            return wxpy(n, alpha, (const double *)dx, (const double *)dy, (double *)dw, stream);
     }
     HostPipe &p = g_pipe[dp->device];
     std::lock_guard<std::mutex> lk(p.mu);

@@ -150,6 +150,7 @@ def test_host_entry_validation_before_cuda(lib):
     assert lib.wxpy_host(-1, 1.0, BASE, BASE + 4096, BASE + 8192, None) == wx.WXPY_EINVAL
     assert lib.wxpy_host(10, 1.0, BASE, BASE + 4096, BASE + 8, None) == wx.WXPY_EOVERLAP
     assert lib.wxpy_host(0, 1.0, None, None, None, None) == 0
-    for bad in ((100, 3), (4096 + 8, 3), (4096, 0), (4096, 9)):
+    for bad in ((100, 3, 0), (4096 + 8, 3, 0), (4096, 0, 0), (4096, 9, 0), (4096, 3, 2)):
         assert lib.wxpy_host_config(*bad) == wx.WXPY_EINVAL
-    assert lib.wxpy_host_config(1 << 22, 3) == 0
+    assert lib.wxpy_host_config(1 << 22, 3, 1) == 0
+    assert lib.wxpy_host_config(1 << 22, 3, 0) == 0

@@ -15,7 +15,23 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _config():
     yield
-    wx.wxpy_host_config(1 << 22, 3)
+    wx.wxpy_host_config(1 << 22, 3, False)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_direct_strategy(pinned):
+    """Zero-copy on mapped pinned memory; pageable memory falls back to staging."""
+    wx.wxpy_host_config(1 << 22, 3, True)
+    for n in (1, 1001, (1 << 20) + 5):
+        alpha, xh, yh, x, y, w = host_arrays(n, 900 + n, pinned)
+        wx.wxpy_host(alpha, x, y, w)
+        torch.cuda.synchronize()
+        want = oracle.wxpy(alpha, xh, yh)
+        assert np.array_equal(w.numpy().view(np.uint64), want.view(np.uint64)), n
+    alpha, xh, yh, x, y, w = host_arrays(70001, 901, pinned)
+    wx.wxpy_host(alpha, x, y, x)  # in place
+    torch.cuda.synchronize()
+    assert np.array_equal(x.numpy().view(np.uint64), oracle.wxpy(alpha, xh, yh).view(np.uint64))
 
 
 def host_arrays(n, seed, pinned):
@@ -34,7 +50,7 @@ def host_arrays(n, seed, pinned):
 @pytest.mark.parametrize("slots", [1, 2, 3])
 def test_chunked_pipeline_matches_oracle(pinned, slots):
     chunk = 4096
-    wx.wxpy_host_config(chunk, slots)
+    wx.wxpy_host_config(chunk, slots, False)
     for n in (1, 5, chunk - 1, chunk, chunk + 1, 3 * chunk + 7, 10 * chunk + 3):
         alpha, xh, yh, x, y, w = host_arrays(n, 500 + n, pinned)
         wx.wxpy_host(alpha, x, y, w)
