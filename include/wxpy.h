@@ -429,6 +429,7 @@ typedef struct wxpy_server_stats {
     int64_t submitted, rejected, completed, failed;
     int64_t queued_now, resident_now, max_queue;
     int64_t batches, launches, elements_done, arena_used;
+    int64_t max_inflight; /* most batches on the device at the same time */
     double mean_batch;   /* requests per batch */
     double window_s;     /* time since the statistics were last reset */
     double p50_s, p99_s, mean_s, max_s; /* submit -> completion, completed requests */

@@ -217,6 +217,7 @@ struct wxpy_server {
     Clock::time_point t_reset;
     int64_t submitted = 0, rejected = 0, completed = 0, failed = 0, max_queue = 0;
     int64_t batches = 0, launches = 0, elements_done = 0, requests_launched = 0;
+    int64_t max_inflight = 0;  // most batches on the device at once
     std::vector<double> latencies;
 
     std::thread sched;
@@ -408,6 +409,9 @@ void scheduler(wxpy_server *sv) {
                 sv->admitted.erase(sv->admitted.begin(), sv->admitted.begin() + taken);
                 if (!batch.empty()) {
                     s.busy = true;
+                    int64_t inflight = 0;
+                    for (const Slot &o : sv->slots) inflight += o.busy ? 1 : 0;
+                    sv->max_inflight = std::max(sv->max_inflight, inflight);
                     ++sv->batches;
                     sv->requests_launched += (int64_t)batch.size();
                 }
@@ -603,6 +607,7 @@ int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
     out->mean_batch = sv->batches ? (double)sv->requests_launched / (double)sv->batches : 0.0;
     out->elements_done = sv->elements_done;
     out->arena_used = sv->arena.used();
+    out->max_inflight = sv->max_inflight;
     out->window_s = seconds(Clock::now() - sv->t_reset);
     out->p50_s = percentile(sv->latencies, 0.50);
     out->p99_s = percentile(sv->latencies, 0.99);
@@ -616,6 +621,7 @@ int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
     if (reset) {
         sv->submitted = sv->rejected = sv->completed = sv->failed = 0;
         sv->batches = sv->launches = sv->elements_done = sv->requests_launched = 0;
+        sv->max_inflight = 0;
         sv->max_queue = (int64_t)sv->queue.size();
         sv->latencies.clear();
         sv->t_reset = Clock::now();

@@ -23,7 +23,7 @@ class ServerConfig(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "submitted", "rejected", "completed", "failed", "queued_now", "resident_now",
-        "max_queue", "batches", "launches", "elements_done", "arena_used")] + \
+        "max_queue", "batches", "launches", "elements_done", "arena_used", "max_inflight")] + \
         [(f, ctypes.c_double) for f in ("mean_batch", "window_s", "p50_s", "p99_s", "mean_s",
                                         "max_s")]
 

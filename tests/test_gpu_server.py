@@ -153,3 +153,16 @@ def test_poisson_loadgen_short():
         assert r["elem_per_s"] > 0
         st = sv.stats()
         assert st["resident_now"] == 0 and st["arena_used"] == 0
+
+
+def test_batches_overlap_under_load():
+    """Continuous batching, not a queue drained batch by batch: with two streams
+    and a steady stream of large requests, two batches are on the device at once
+    while new requests keep being admitted."""
+    with Server(budget_bytes=4 << 30, n_streams=2, max_batch=64) as sv:
+        r = sv.loadgen(rate=20000.0, duration_s=0.5, n_min=1 << 18, n_max=1 << 22, seed=11,
+                       drain_timeout_s=30.0)
+        st = sv.stats()
+        assert r["drained"] == 1 and r["failed"] == 0
+        assert st["max_inflight"] == 2
+        assert st["batches"] > 2 and st["completed"] == r["completed"]
