@@ -102,6 +102,92 @@ def wxpy(alpha: float, x: np.ndarray, y: np.ndarray,
     return wxpy_into(alpha, x, y, w, library)
 
 
+# ---------------------------------------------------------------- sibling kernels
+VEC_SOURCE = os.path.join(HERE, "vecops_oracle.c")
+VEC_LIBRARY = os.path.join(HERE, "liboracle_vecops.so")
+_vec_lib = None
+
+
+def load_vec_library(path: str) -> ctypes.CDLL:
+    """Load an oracle library built from ``vecops_oracle.c`` (or a copy)."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    L = ctypes.CDLL(path)
+    i64, d = ctypes.c_int64, ctypes.c_double
+    for name, args in (("oracle_axpy", [i64, d, dp, dp]), ("oracle_aypx", [i64, d, dp, dp]),
+                       ("oracle_axpbypcz", [i64, d, d, d, dp, dp, dp]),
+                       ("oracle_maxpy", [i64, ctypes.c_int, dp, ctypes.POINTER(dp), dp]),
+                       ("oracle_pmult", [i64, dp, dp, dp])):
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = args
+    return L
+
+
+def vec_lib() -> ctypes.CDLL:
+    """The sibling-kernel oracle library, built on first use."""
+    global _vec_lib
+    with _lock:
+        if _vec_lib is None:
+            _vec_lib = load_vec_library(build(source=VEC_SOURCE, output=VEC_LIBRARY))
+        return _vec_lib
+
+
+def _vcheck(rc, name):
+    if rc != 0:
+        raise RuntimeError(f"{name} returned {rc}")
+
+
+def axpy(alpha, x, y, library=None):
+    """A new array: RN(RN(alpha*x) + y) (PETSc VecAXPY on a copy of y)."""
+    out = np.array(y, dtype=np.float64, copy=True)
+    _check(np.ascontiguousarray(x), "x")
+    L = library or vec_lib()
+    _vcheck(L.oracle_axpy(out.shape[0], float(alpha), _dptr(np.ascontiguousarray(x)), _dptr(out)),
+            "oracle_axpy")
+    return out
+
+
+def aypx(alpha, x, y, library=None):
+    """A new array: RN(x + RN(alpha*y)) (PETSc VecAYPX on a copy of y)."""
+    out = np.array(y, dtype=np.float64, copy=True)
+    L = library or vec_lib()
+    _vcheck(L.oracle_aypx(out.shape[0], float(alpha), _dptr(np.ascontiguousarray(x)), _dptr(out)),
+            "oracle_aypx")
+    return out
+
+
+def axpbypcz(alpha, beta, gamma, x, y, z, library=None):
+    """A new array: RN(RN(RN(alpha*x) + RN(beta*y)) + RN(gamma*z)) (VecAXPBYPCZ on a copy of z)."""
+    out = np.array(z, dtype=np.float64, copy=True)
+    L = library or vec_lib()
+    _vcheck(L.oracle_axpbypcz(out.shape[0], float(alpha), float(beta), float(gamma),
+                              _dptr(np.ascontiguousarray(x)), _dptr(np.ascontiguousarray(y)),
+                              _dptr(out)), "oracle_axpbypcz")
+    return out
+
+
+def maxpy(alphas, xs, y, library=None):
+    """A new array: y + sum_j alpha_j x_j, each product and each sum rounded, j in order."""
+    out = np.array(y, dtype=np.float64, copy=True)
+    xs = [np.ascontiguousarray(x, dtype=np.float64) for x in xs]
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptrs = (dp * max(1, len(xs)))(*[_dptr(x) for x in xs])
+    L = library or vec_lib()
+    _vcheck(L.oracle_maxpy(out.shape[0], len(xs), _dptr(al), ptrs, _dptr(out)), "oracle_maxpy")
+    return out
+
+
+def pmult(x, y, library=None):
+    """A new array: RN(x*y) element-wise (PETSc VecPointwiseMult)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    L = library or vec_lib()
+    _vcheck(L.oracle_pmult(x.shape[0], _dptr(x), _dptr(np.ascontiguousarray(y)), _dptr(out)),
+            "oracle_pmult")
+    return out
+
+
 def wxpy_batch(alphas, xs, ys, library: ctypes.CDLL | None = None):
     """Batched oracle: one output array per segment (a list)."""
     count = len(xs)
