@@ -403,6 +403,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
         result["batched"] = measure_batched(wx, lib, torch, dev, sh, stream, peak)
+        result["vecops"] = measure_vecops(wx, torch, dev, stream, peak)
         if args.serve_seconds > 0:
             result["served"] = measure_served(args.serve_seconds)
     if rank == 0:
@@ -642,6 +643,49 @@ def measure_batched(wx, lib, torch, dev, sh, stream, peak, reps=20, per_call_rep
                        "mixed_gbs": tune["mixed_gbs"],
                        "shapes": {r["bucket"]: [r["tile_elems"], r["unroll"]]
                                   for r in tune["buckets"]}}}
+
+
+def measure_vecops(wx, torch, dev, stream, peak, reps=10):
+    """The sibling vector kernels at n = 2^26 (512 MiB per vector): GB/s of
+    algorithmic bytes (axpy, aypx, pointwise_mult 24 B/element, axpbypcz 32,
+    maxpy with m = 4: 48), for each FP64-offload setting where it applies."""
+    n = 1 << 26
+    v = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    for k, t in enumerate(v):
+        wx.wxpy_fill_uniform(t, 100 + k, 1)
+    al4 = [0.25, -0.5, 0.75, 1.0]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def row(name, nbytes, ms, **kw):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        return dict(op=name, gbs=gbs, frac_of_peak=gbs / peak, **kw)
+
+    out = [row("axpy", 24 * n, timed(lambda: wx.wxpy_axpy(0.5, v[0], v[1]))),
+           row("aypx", 24 * n, timed(lambda: wx.wxpy_aypx(0.5, v[0], v[1]))),
+           row("pointwise_mult", 24 * n, timed(lambda: wx.wxpy_pointwise_mult(v[0], v[1], v[2])))]
+    for of in (0, 1, 2):
+        wx.wxpy_vecops_offload(of)
+        out.append(row("axpbypcz", 32 * n,
+                       timed(lambda: wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])),
+                       fp64_offload=of))
+        out.append(row("maxpy_m4", 48 * n,
+                       timed(lambda: wx.wxpy_maxpy(al4, [v[0], v[1], v[2], v[4]], v[3])),
+                       fp64_offload=of))
+    wx.wxpy_vecops_offload(2)
+    del v
+    torch.cuda.empty_cache()
+    return {"n": n, "reps": reps, "results": out}
 
 
 SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)

@@ -202,6 +202,37 @@ int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,
 int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
                    double *w, void *stream);
 
+/* ---- sibling vector kernels of the same library -------------------------------- */
+
+/* The paper tunes vecwxpy (Sec. 3, Fig. 1); these are its PETSc siblings, on
+ * the same conventions (device pointers, asynchronous on `stream`, 8-byte
+ * alignment, the output either disjoint from or exactly equal to each input,
+ * WXPY_EINVAL / WXPY_EOVERLAP / WXPY_ECUDA as for wxpy()).  Each product and
+ * each sum is rounded to nearest-even in binary64, left to right, never fused:
+ *
+ *   wxpy_axpy:           y[i] = RN(RN(alpha*x[i]) + y[i])         (VecAXPY; = wxpy into y)
+ *   wxpy_aypx:           y[i] = RN(x[i] + RN(alpha*y[i]))         (VecAYPX; = wxpy(alpha, y, x) into y)
+ *   wxpy_axpbypcz:       z[i] = RN(RN(RN(alpha*x[i]) + RN(beta*y[i])) + RN(gamma*z[i]))
+ *   wxpy_maxpy:          y[i] = RN(..RN(RN(y[i] + RN(a[0]*x[0][i])) + RN(a[1]*x[1][i])).. + RN(a[m-1]*x[m-1][i]))
+ *   wxpy_pointwise_mult: w[i] = RN(x[i]*y[i])                     (VecPointwiseMult)
+ *
+ * axpy and aypx run the tuned wxpy() variants.  The others are one streaming
+ * kernel each (32-byte accesses when all pointers share their offset mod 32);
+ * maxpy takes `alpha` (m values) and `x` (m device pointers) as HOST arrays and
+ * makes one launch per group of 8 terms. */
+int wxpy_axpy(int64_t n, double alpha, const double *x, double *y, void *stream);
+int wxpy_aypx(int64_t n, double alpha, const double *x, double *y, void *stream);
+int wxpy_axpbypcz(int64_t n, double alpha, double beta, double gamma, const double *x,
+                  const double *y, double *z, void *stream);
+int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, double *y,
+               void *stream);
+int wxpy_pointwise_mult(int64_t n, const double *x, const double *y, double *w, void *stream);
+
+/* How many of the sums of axpbypcz and maxpy run as the exactly rounded
+ * integer-pipeline addition (see wxpy_variant_info.fp64_offload): 0 none,
+ * 1 every other one, 2 all (default).  Same bits in every case. */
+int wxpy_vecops_offload(int offload);
+
 /* ---- batched launch: many independent problems in one launch ----------------- */
 
 /* One problem of a batch: w = RN(RN(alpha*x) + y) over n elements (Sec. 3,

@@ -113,6 +113,12 @@ SIGNATURES = {
     "wxpy_batch_shape_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_batch_shape_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_batch_shape_reset": (_INT, []),
+    "wxpy_axpy": (_INT, [_I64, _D, _P, _P, _P]),
+    "wxpy_aypx": (_INT, [_I64, _D, _P, _P, _P]),
+    "wxpy_axpbypcz": (_INT, [_I64, _D, _D, _D, _P, _P, _P, _P]),
+    "wxpy_maxpy": (_INT, [_I64, _INT, ctypes.POINTER(_D), ctypes.POINTER(_P), _P, _P]),
+    "wxpy_pointwise_mult": (_INT, [_I64, _P, _P, _P, _P]),
+    "wxpy_vecops_offload": (_INT, [_INT]),
     "wxpy_host": (_INT, [_I64, _D, _P, _P, _P, _P]),
     "wxpy_host_config": (_INT, [_I64, _INT, _INT]),
     "wxpy_batch_launch_get": (_INT, [ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
@@ -259,6 +265,72 @@ def wxpy(alpha: float, x, y, w=None, stream=None):
     n, a, px, py, pw, w = _prepare(alpha, x, y, w)
     check(lib().wxpy(n, a, px, py, pw, _stream_handle(stream)), "wxpy")
     return w
+
+
+def wxpy_axpy(alpha: float, x, y, stream=None):
+    """y <- alpha*x + y in place (VecAXPY)."""
+    n, px = _vec(x, "x")
+    ny, py = _vec(y, "y")
+    if n != ny:
+        raise ValueError("length mismatch")
+    check(lib().wxpy_axpy(n, float(alpha), px, py, _stream_handle(stream)), "wxpy_axpy")
+    return y
+
+
+def wxpy_aypx(alpha: float, x, y, stream=None):
+    """y <- x + alpha*y in place (VecAYPX)."""
+    n, px = _vec(x, "x")
+    ny, py = _vec(y, "y")
+    if n != ny:
+        raise ValueError("length mismatch")
+    check(lib().wxpy_aypx(n, float(alpha), px, py, _stream_handle(stream)), "wxpy_aypx")
+    return y
+
+
+def wxpy_axpbypcz(alpha: float, beta: float, gamma: float, x, y, z, stream=None):
+    """z <- alpha*x + beta*y + gamma*z in place (VecAXPBYPCZ)."""
+    n, px = _vec(x, "x")
+    _, py = _vec(y, "y")
+    nz, pz = _vec(z, "z")
+    if not (n == y.numel() == nz):
+        raise ValueError("length mismatch")
+    check(lib().wxpy_axpbypcz(n, float(alpha), float(beta), float(gamma), px, py, pz,
+                              _stream_handle(stream)), "wxpy_axpbypcz")
+    return z
+
+
+def wxpy_maxpy(alphas, xs, y, stream=None):
+    """y <- y + sum_j alphas[j]*xs[j] in place, terms in order (VecMAXPY)."""
+    n, py = _vec(y, "y")
+    ptrs = []
+    for j, x in enumerate(xs):
+        m, p = _vec(x, f"x[{j}]")
+        if m != n:
+            raise ValueError("length mismatch")
+        ptrs.append(p)
+    m = len(ptrs)
+    al = (_D * max(1, m))(*[float(a) for a in alphas])
+    pp = (_P * max(1, m))(*ptrs)
+    check(lib().wxpy_maxpy(n, m, al, pp, py, _stream_handle(stream)), "wxpy_maxpy")
+    return y
+
+
+def wxpy_pointwise_mult(x, y, w=None, stream=None):
+    """w <- x .* y (VecPointwiseMult)."""
+    import torch
+    n, px = _vec(x, "x")
+    _, py = _vec(y, "y")
+    if w is None:
+        w = torch.empty_like(x)
+    nw, pw = _vec(w, "w")
+    if not (n == y.numel() == nw):
+        raise ValueError("length mismatch")
+    check(lib().wxpy_pointwise_mult(n, px, py, pw, _stream_handle(stream)), "wxpy_pointwise_mult")
+    return w
+
+
+def wxpy_vecops_offload(offload: int) -> None:
+    check(lib().wxpy_vecops_offload(offload), "wxpy_vecops_offload")
 
 
 def _host_vec(t, name: str):

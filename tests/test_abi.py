@@ -154,3 +154,20 @@ def test_host_entry_validation_before_cuda(lib):
         assert lib.wxpy_host_config(*bad) == wx.WXPY_EINVAL
     assert lib.wxpy_host_config(1 << 22, 3, 1) == 0
     assert lib.wxpy_host_config(1 << 22, 3, 0) == 0
+
+
+def test_vecops_validation_before_cuda(lib):
+    import ctypes
+    P = ctypes.c_void_p
+    assert lib.wxpy_axpbypcz(-1, 1.0, 1.0, 1.0, BASE, BASE + 4096, BASE + 8192, None) == wx.WXPY_EINVAL
+    assert lib.wxpy_axpbypcz(10, 1.0, 1.0, 1.0, BASE, BASE + 4096, BASE + 8, None) == wx.WXPY_EOVERLAP
+    assert lib.wxpy_axpbypcz(10, 1.0, 1.0, 1.0, BASE, BASE + 4, BASE + 8192, None) == wx.WXPY_EINVAL
+    assert lib.wxpy_pointwise_mult(10, BASE, BASE + 4096, BASE + 4096 + 16, None) == wx.WXPY_EOVERLAP
+    assert lib.wxpy_pointwise_mult(0, None, None, None, None) == 0
+    al = (ctypes.c_double * 2)(1.0, 2.0)
+    xs = (P * 2)(BASE, BASE + 8)  # x[1] overlaps y partially
+    assert lib.wxpy_maxpy(10, 2, al, xs, BASE + 16, None) == wx.WXPY_EOVERLAP
+    assert lib.wxpy_maxpy(10, -1, al, xs, BASE + 65536, None) == wx.WXPY_EINVAL
+    assert lib.wxpy_axpy(-1, 1.0, BASE, BASE + 4096, None) == wx.WXPY_EINVAL
+    assert lib.wxpy_vecops_offload(3) == wx.WXPY_EINVAL
+    assert lib.wxpy_vecops_offload(2) == 0
