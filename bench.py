@@ -648,12 +648,13 @@ def measure_batched(wx, lib, torch, dev, sh, stream, peak, reps=20, per_call_rep
 def measure_vecops(wx, torch, dev, stream, peak, reps=10):
     """The sibling vector kernels at n = 2^26 (512 MiB per vector): GB/s of
     algorithmic bytes (axpy, aypx, pointwise_mult 24 B/element, axpbypcz 32,
-    maxpy with m = 4: 48), for each FP64-offload setting where it applies."""
+    maxpy with m terms 8(m + 2)) under each operation's default pipe split,
+    then axpbypcz and maxpy (m = 4, 8) under a few other splits (add offload,
+    product sixteenths) to show what the split buys."""
     n = 1 << 26
-    v = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    v = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(10)]
     for k, t in enumerate(v):
         wx.wxpy_fill_uniform(t, 100 + k, 1)
-    al4 = [0.25, -0.5, 0.75, 1.0]
 
     def timed(fn):
         for _ in range(2):
@@ -671,21 +672,34 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
         gbs = nbytes / (ms / 1e3) / 1e9
         return dict(op=name, gbs=gbs, frac_of_peak=gbs / peak, **kw)
 
+    def maxpy(m):
+        al = [0.25 * (j + 1) for j in range(m)]
+        return lambda: wx.wxpy_maxpy(al, v[1:m + 1], v[0])
+
+    axpbypcz = lambda: wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])
+    wx.wxpy_vecops_pipes(-1, -1)
     out = [row("axpy", 24 * n, timed(lambda: wx.wxpy_axpy(0.5, v[0], v[1]))),
            row("aypx", 24 * n, timed(lambda: wx.wxpy_aypx(0.5, v[0], v[1]))),
-           row("pointwise_mult", 24 * n, timed(lambda: wx.wxpy_pointwise_mult(v[0], v[1], v[2])))]
-    for of in (0, 1, 2):
-        wx.wxpy_vecops_offload(of)
-        out.append(row("axpbypcz", 32 * n,
-                       timed(lambda: wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])),
-                       fp64_offload=of))
-        out.append(row("maxpy_m4", 48 * n,
-                       timed(lambda: wx.wxpy_maxpy(al4, [v[0], v[1], v[2], v[4]], v[3])),
-                       fp64_offload=of))
-    wx.wxpy_vecops_offload(2)
+           row("pointwise_mult", 24 * n, timed(lambda: wx.wxpy_pointwise_mult(v[0], v[1], v[2]))),
+           row("axpbypcz", 32 * n, timed(axpbypcz))]
+    for m in (1, 2, 4, 8):
+        out.append(row(f"maxpy_m{m}", 8 * (m + 2) * n, timed(maxpy(m))))
+    splits = []
+    for add, mul in ((0, 0), (1, 0), (2, 0), (0, 8), (0, 16)):
+        wx.wxpy_vecops_pipes(add, mul)
+        splits.append(row("axpbypcz", 32 * n, timed(axpbypcz), add_offload=add, mul_sixteenths=mul))
+        for m in (4, 8):
+            splits.append(row(f"maxpy_m{m}", 8 * (m + 2) * n, timed(maxpy(m)),
+                              add_offload=add, mul_sixteenths=mul))
+    wx.wxpy_vecops_pipes(-1, -1)
+    status = "ok"
+    try:
+        wx.wxpy_vecops_status()
+    except wx.WxpyError as e:
+        status = str(e)
     del v
     torch.cuda.empty_cache()
-    return {"n": n, "reps": reps, "results": out}
+    return {"n": n, "reps": reps, "defaults": out, "splits": splits, "wait_status": status}
 
 
 SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)

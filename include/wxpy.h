@@ -216,10 +216,14 @@ int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
  *   wxpy_maxpy:          y[i] = RN(..RN(RN(y[i] + RN(a[0]*x[0][i])) + RN(a[1]*x[1][i])).. + RN(a[m-1]*x[m-1][i]))
  *   wxpy_pointwise_mult: w[i] = RN(x[i]*y[i])                     (VecPointwiseMult)
  *
- * axpy and aypx run the tuned wxpy() variants.  The others are one streaming
- * kernel each (32-byte accesses when all pointers share their offset mod 32);
- * maxpy takes `alpha` (m values) and `x` (m device pointers) as HOST arrays and
- * makes one launch per group of 8 terms. */
+ * axpy and aypx run the tuned wxpy() variants.  When all pointers share their
+ * offset mod 32 bytes, axpbypcz and maxpy stream their inputs through a
+ * shared-memory ring filled by bulk asynchronous copies (one producer warp,
+ * eight consumer warps per block, persistent grid; see wxpy_vecops_status)
+ * and pointwise_mult loads 32 bytes per thread into registers; otherwise all
+ * three take one element per thread.  maxpy takes `alpha` (m values) and `x`
+ * (m device pointers) as HOST arrays and makes one launch per group of 8
+ * terms, in order. */
 int wxpy_axpy(int64_t n, double alpha, const double *x, double *y, void *stream);
 int wxpy_aypx(int64_t n, double alpha, const double *x, double *y, void *stream);
 int wxpy_axpbypcz(int64_t n, double alpha, double beta, double gamma, const double *x,
@@ -228,10 +232,26 @@ int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, do
                void *stream);
 int wxpy_pointwise_mult(int64_t n, const double *x, const double *y, double *w, void *stream);
 
-/* How many of the sums of axpbypcz and maxpy run as the exactly rounded
- * integer-pipeline addition (see wxpy_variant_info.fp64_offload): 0 none,
- * 1 every other one, 2 all (default).  Same bits in every case. */
-int wxpy_vecops_offload(int offload);
+/* Pipe split of the streaming sibling kernels (axpbypcz, maxpy,
+ * pointwise_mult): how much of their binary64 arithmetic runs as the exactly
+ * rounded integer-pipeline operations instead of FP64 instructions.
+ * add_offload: the sums (0 none, 1 every other one, 2 all); mul_sixteenths:
+ * the fraction, in sixteenths, of each warp's loop iterations whose products
+ * run there (0..16).  -1 in either restores that operation's default (sums
+ * in FP64; products 14/16 for axpbypcz, 13/16 for maxpy groups of 2 terms,
+ * 16/16 for groups of 3..8, 4/16 for pointwise_mult; a maxpy group of one
+ * term runs as wxpy() and its tuned variant).  The bits of every
+ * result are the same under every split; only the speed differs.  Process-
+ * wide, read at each call.  Errors: WXPY_EINVAL out of range. */
+int wxpy_vecops_pipes(int add_offload, int mul_sixteenths);
+
+/* axpbypcz, maxpy and pointwise_mult on 32-byte co-aligned pointers stream
+ * their inputs into shared memory with bulk asynchronous copies, completed on
+ * mbarriers; every wait on those barriers gives up after one second.  This
+ * synchronises the current device, then returns WXPY_ETIMEOUT (and clears
+ * the record) if a wait of any such kernel on it ran out since the last
+ * call -- that kernel's output is then incomplete -- else WXPY_OK. */
+int wxpy_vecops_status(void);
 
 /* ---- batched launch: many independent problems in one launch ----------------- */
 
@@ -556,6 +576,12 @@ int wxpy_fill_uniform(int64_t n, uint64_t seed, uint32_t tag, int64_t start,
  * cudaError_t `cuda_error` (returned as WXPY_ECUDA) without touching the GPU.
  * count = 0 clears it.  Process-wide. */
 int wxpy_debug_inject_launch_error(int cuda_error, int count);
+
+/* Staged vector kernels launched after this call stop issuing copies at tile
+ * `tile` (in the block that owns it), so that block's consumers' bounded wait
+ * runs out and wxpy_vecops_status() reports WXPY_ETIMEOUT; no copy is left in
+ * flight.  -1 (the default) turns it off.  Process-wide. */
+int wxpy_debug_vecops_drop_tile(int64_t tile);
 
 #ifdef __cplusplus
 }

@@ -118,7 +118,9 @@ SIGNATURES = {
     "wxpy_axpbypcz": (_INT, [_I64, _D, _D, _D, _P, _P, _P, _P]),
     "wxpy_maxpy": (_INT, [_I64, _INT, ctypes.POINTER(_D), ctypes.POINTER(_P), _P, _P]),
     "wxpy_pointwise_mult": (_INT, [_I64, _P, _P, _P, _P]),
-    "wxpy_vecops_offload": (_INT, [_INT]),
+    "wxpy_vecops_pipes": (_INT, [_INT, _INT]),
+    "wxpy_vecops_status": (_INT, []),
+    "wxpy_debug_vecops_drop_tile": (_INT, [_I64]),
     "wxpy_host": (_INT, [_I64, _D, _P, _P, _P, _P]),
     "wxpy_host_config": (_INT, [_I64, _INT, _INT]),
     "wxpy_batch_launch_get": (_INT, [ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
@@ -329,8 +331,18 @@ def wxpy_pointwise_mult(x, y, w=None, stream=None):
     return w
 
 
-def wxpy_vecops_offload(offload: int) -> None:
-    check(lib().wxpy_vecops_offload(offload), "wxpy_vecops_offload")
+def wxpy_vecops_pipes(add_offload: int = -1, mul_sixteenths: int = -1) -> None:
+    """Pipe split of axpbypcz / maxpy / pointwise_mult (-1: the operation's default)."""
+    check(lib().wxpy_vecops_pipes(add_offload, mul_sixteenths), "wxpy_vecops_pipes")
+
+
+def wxpy_vecops_status() -> None:
+    """Raises WxpyError(WXPY_ETIMEOUT) when a staged vector kernel's bounded wait ran out."""
+    check(lib().wxpy_vecops_status(), "wxpy_vecops_status")
+
+
+def wxpy_debug_vecops_drop_tile(tile: int) -> None:
+    check(lib().wxpy_debug_vecops_drop_tile(tile), "wxpy_debug_vecops_drop_tile")
 
 
 def _host_vec(t, name: str):

@@ -169,5 +169,9 @@ def test_vecops_validation_before_cuda(lib):
     assert lib.wxpy_maxpy(10, 2, al, xs, BASE + 16, None) == wx.WXPY_EOVERLAP
     assert lib.wxpy_maxpy(10, -1, al, xs, BASE + 65536, None) == wx.WXPY_EINVAL
     assert lib.wxpy_axpy(-1, 1.0, BASE, BASE + 4096, None) == wx.WXPY_EINVAL
-    assert lib.wxpy_vecops_offload(3) == wx.WXPY_EINVAL
-    assert lib.wxpy_vecops_offload(2) == 0
+    for bad in ((3, 0), (-2, 0), (0, 17), (0, -2)):
+        assert lib.wxpy_vecops_pipes(*bad) == wx.WXPY_EINVAL
+    assert lib.wxpy_vecops_pipes(2, 16) == 0
+    assert lib.wxpy_vecops_pipes(-1, -1) == 0
+    assert lib.wxpy_debug_vecops_drop_tile(-2) == wx.WXPY_EINVAL
+    assert lib.wxpy_debug_vecops_drop_tile(-1) == 0

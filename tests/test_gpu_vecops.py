@@ -1,7 +1,8 @@
 """GPU parity of the sibling vector kernels (VecAXPY, VecAYPX, VecAXPBYPCZ,
 VecMAXPY, VecPointwiseMult) through the C ABI: bitwise against the oracle of
-vecops_oracle.c, for every FP64-offload setting, alignment class and in-place
-form; guard canaries around every buffer."""
+vecops_oracle.c, for pipe splits from all-FP64 to all-integer (sums and
+products), every alignment class and in-place form; guard canaries around
+every buffer."""
 import numpy as np
 import pytest
 import torch
@@ -14,13 +15,20 @@ from test_vecops_oracle import wide
 
 pytestmark = pytest.mark.gpu
 
-SIZES = (1, 3, 67, 4099, 262147)
+# up to about 3M elements: several tiles per block of the persistent staged
+# grid, so every block wraps around its shared-memory ring more than once
+SIZES = (1, 3, 67, 4099, 262147, 3000007)
+
+
+# (add offload, product sixteenths): FP64 only, each integer path alone and
+# mixed, all-integer, and the defaults (-1, -1)
+SPLITS = [(0, 0), (1, 0), (2, 0), (0, 16), (0, 9), (1, 5), (2, 16), (-1, -1)]
 
 
 @pytest.fixture(autouse=True)
-def _offload():
+def _pipes():
     yield
-    wx.wxpy_vecops_offload(2)
+    wx.wxpy_vecops_pipes(-1, -1)
 
 
 def vals(seed, n, special):
@@ -37,10 +45,10 @@ def same(got_dev, want):
 
 
 @pytest.mark.parametrize("special", [False, True])
-@pytest.mark.parametrize("offload", [0, 1, 2])
+@pytest.mark.parametrize("split", SPLITS)
 @pytest.mark.parametrize("offs", [(0, 0, 0), (8, 8, 8), (24, 24, 24), (0, 8, 24)])
-def test_axpbypcz(offload, offs, special):
-    wx.wxpy_vecops_offload(offload)
+def test_axpbypcz(split, offs, special):
+    wx.wxpy_vecops_pipes(*split)
     for n in SIZES:
         xh, yh, zh = (vals(10 * n + k, n, special) for k in range(3))
         gx, gy, gz = Guarded(n, offs[0]).set(xh), Guarded(n, offs[1]).set(yh), Guarded(n, offs[2]).set(zh)
@@ -52,11 +60,11 @@ def test_axpbypcz(offload, offs, special):
             g.check()
 
 
-@pytest.mark.parametrize("offload", [0, 1, 2])
+@pytest.mark.parametrize("split", SPLITS)
 @pytest.mark.parametrize("m", [0, 1, 3, 8, 9, 17])
-def test_maxpy(offload, m):
-    wx.wxpy_vecops_offload(offload)
-    for n in (5, 4099, 70001):
+def test_maxpy(split, m):
+    wx.wxpy_vecops_pipes(*split)
+    for n in (5, 4099, 70001, 2000003):
         for special in (False, True):
             yh = vals(7 + n, n, special)
             xsh = [vals(100 + 13 * j + n, n, special) for j in range(m)]
@@ -71,7 +79,9 @@ def test_maxpy(offload, m):
 
 
 @pytest.mark.parametrize("special", [False, True])
-def test_pointwise_mult_and_in_place(special):
+@pytest.mark.parametrize("mul", [-1, 16, 7])
+def test_pointwise_mult_and_in_place(special, mul):
+    wx.wxpy_vecops_pipes(-1, mul)
     for n in SIZES:
         xh, yh = vals(n, n, special), vals(n + 1, n, special)
         gx, gy, gw = Guarded(n, 8).set(xh), Guarded(n, 8).set(yh), Guarded(n, 24)
@@ -83,6 +93,104 @@ def test_pointwise_mult_and_in_place(special):
         assert same(gx.t, oracle.pmult(xh, yh))
         for g in (gx, gy, gw):
             g.check()
+
+
+def _product_pairs():
+    """(x, y) pairs aimed at the integer-pipeline product: ties to even (odd
+    significands times 3/2 and 3/4), products just below and above a power of
+    two (the significand product on either side of 2^105, rounding carries
+    into the next binade), results at the subnormal and overflow boundaries,
+    zeros, subnormals, inf and NaN, and random significands over the whole
+    exponent range."""
+    import pins
+    xs, ys = [], []
+    ulp = 2.0 ** -52
+    sig = [1.0, 1.0 + ulp, 1.5, 1.5 + ulp, 2.0 - ulp, 2.0 - 2 * ulp, 1.25, 1.75 - ulp,
+           1.0 + 3 * ulp, 1.4142135623730951, 1.0000000149011612]
+    for k in range(1, 4000, 31):  # ties: odd significand times 3/2, 3/4
+        xs += [1.0 + k * ulp, -(1.0 + k * ulp), 1.0 + k * ulp]
+        ys += [1.5, 1.5, -0.75]
+    for a in sig:
+        for b in sig:
+            for ea, eb in ((0, 0), (0, 1), (-1, 0), (500, -500), (3, -7)):
+                xs.append(np.ldexp(a, ea))
+                ys.append(np.ldexp(b, eb))
+    # the subnormal boundary (results near 2^-1022) and the overflow one (near 2^1024)
+    for a in sig:
+        for b in sig:
+            for ea in (-1022, -600, -511, 0, 511, 600, 1023):
+                for d in (-2, -1, 0, 1):
+                    eb = -1022 - ea + d
+                    if -1074 <= eb <= 1023:
+                        xs.append(np.ldexp(a, ea))
+                        ys.append(np.ldexp(b, eb))
+                    eb2 = 1023 - ea + d
+                    if -1074 <= eb2 <= 1023:
+                        xs.append(np.ldexp(a, ea))
+                        ys.append(np.ldexp(b, eb2))
+    sv = pins.special_values()
+    for a in sv:
+        for b in sv:
+            xs.append(a)
+            ys.append(b)
+    rng = np.random.default_rng(5)
+    m = 20000
+    r = rng.uniform(1.0, 2.0, (2, m)) * rng.choice([-1.0, 1.0], (2, m))
+    e = rng.integers(-540, 540, (2, m))
+    xs += list(np.ldexp(r[0], e[0]))
+    ys += list(np.ldexp(r[1], e[1]))
+    with np.errstate(over="ignore"):
+        return np.array(xs, dtype=np.float64), np.array(ys, dtype=np.float64)
+
+
+def test_integer_pipeline_product_is_exact():
+    """Every product in the integer pipeline: the oracle's bits (NaN by class)
+    on inputs chosen to hit every branch of the integer-pipeline product, as
+    pointwise_mult and as the three products of axpbypcz."""
+    xh, yh = _product_pairs()
+    n = len(xh)
+    wx.wxpy_vecops_pipes(0, 16)
+    for off in (0, 8):  # 32-byte path and the scalar one
+        gx, gy, gw = Guarded(n, off).set(xh), Guarded(n, 0).set(yh), Guarded(n, off)
+        wx.wxpy_pointwise_mult(gx.t, gy.t, gw.t)
+        torch.cuda.synchronize()
+        want = oracle.pmult(xh, yh)
+        got = gw.t.cpu().numpy()
+        bad = np.nonzero((got.view(np.uint64) != want.view(np.uint64)) & ~(np.isnan(got) & np.isnan(want)))[0]
+        assert bad.size == 0, (f"{bad.size} differ, first x={xh[bad[0]]!r} y={yh[bad[0]]!r} "
+                               f"got {got[bad[0]].hex()} want {want[bad[0]].hex()}")
+        for g in (gx, gy, gw):
+            g.check()
+    z = np.roll(xh, 7)
+    for a, b, c in ((1.5, -0.75, 1.0 + 2.0 ** -52), (2.0 ** 600, 2.0 ** -600, -3.0)):
+        gx, gy, gz = Guarded(n, 0).set(xh), Guarded(n, 0).set(yh), Guarded(n, 0).set(z)
+        wx.wxpy_axpbypcz(a, b, c, gx.t, gy.t, gz.t)
+        torch.cuda.synchronize()
+        assert same(gz.t, oracle.axpbypcz(a, b, c, xh, yh, z)), (a, b, c)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The producer of the block owning tile 0 stops before copying it: that
+    block's consumers give up after their one-second bound, the host reads
+    WXPY_ETIMEOUT, and the next launch on the same context is exact."""
+    n = 1 << 20
+    xh, yh, zh = (vals(900 + k, n, False) for k in range(3))
+    x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+    z = torch.from_numpy(zh).cuda()
+    wx.wxpy_vecops_status()  # clean start
+    try:
+        wx.wxpy_debug_vecops_drop_tile(0)
+        wx.wxpy_axpbypcz(0.5, 1.5, -2.0, x, y, z)
+        with pytest.raises(wx.WxpyError) as e:
+            wx.wxpy_vecops_status()
+        assert e.value.status == wx.WXPY_ETIMEOUT
+    finally:
+        wx.wxpy_debug_vecops_drop_tile(-1)
+    wx.wxpy_vecops_status()  # the record was cleared
+    z.copy_(torch.from_numpy(zh))
+    wx.wxpy_axpbypcz(0.5, 1.5, -2.0, x, y, z)
+    wx.wxpy_vecops_status()
+    assert same(z, oracle.axpbypcz(0.5, 1.5, -2.0, xh, yh, zh))
 
 
 def test_axpy_aypx_through_the_tuned_path():
