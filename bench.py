@@ -650,7 +650,9 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
     algorithmic bytes (axpy, aypx, pointwise_mult 24 B/element, axpbypcz 32,
     maxpy with m terms 8(m + 2)) under each operation's default pipe split,
     then axpbypcz and maxpy (m = 4, 8) under a few other splits (add offload,
-    product sixteenths) to show what the split buys."""
+    product sixteenths) to show what the split buys.  The pipe-split search
+    (wxpy_vecops_tune, n = 2^24) runs first, so the default rows are the
+    searched splits, as for a user who tuned."""
     n = 1 << 26
     v = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(10)]
     for k, t in enumerate(v):
@@ -678,6 +680,9 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
 
     axpbypcz = lambda: wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])
     wx.wxpy_vecops_pipes(-1, -1)
+    t0 = time.time()
+    search = wx.wxpy_vecops_tune(1 << 24)
+    search_s = time.time() - t0
     out = [row("axpy", 24 * n, timed(lambda: wx.wxpy_axpy(0.5, v[0], v[1]))),
            row("aypx", 24 * n, timed(lambda: wx.wxpy_aypx(0.5, v[0], v[1]))),
            row("pointwise_mult", 24 * n, timed(lambda: wx.wxpy_pointwise_mult(v[0], v[1], v[2]))),
@@ -699,7 +704,11 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
         status = str(e)
     del v
     torch.cuda.empty_cache()
-    return {"n": n, "reps": reps, "defaults": out, "splits": splits, "wait_status": status}
+    return {"n": n, "reps": reps, "defaults": out, "splits": splits, "wait_status": status,
+            "search": {"n": 1 << 24, "seconds": search_s,
+                       "classes": [{k: r[k] for k in ("op", "add_offload", "mul_sixteenths",
+                                                     "candidates", "rejected", "best_us",
+                                                     "default_us", "gbs")} for r in search]}}
 
 
 SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)
@@ -788,9 +797,16 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--variant", type=int, default=-1,
                     help="profiling mode: force this variant id instead of the tuned one")
+    ap.add_argument("--vecop", default="",
+                    help="profiling mode: only run this sibling kernel (axpbypcz, maxpy4, "
+                         "maxpy8, pointwise_mult) on n = SINGLE, --reps times")
+    ap.add_argument("--pipes", default="-1,-1",
+                    help="profiling mode: add offload and product sixteenths for --vecop")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.single and args.vecop:
+        return run_vecop(args)
     if args.single:
         return run_single(args)
     return run_ours(args)
@@ -821,6 +837,34 @@ def run_single(args):
     torch.cuda.synchronize()
     print(json.dumps({"single": n, "reps": args.reps, "variant": v, "source": src,
                       "tuning": tuning}), flush=True)
+    return 0
+
+
+def run_vecop(args):
+    """A small fixed case for ncu captures of a sibling kernel: n = args.single
+    elements per vector from the device generator, args.reps calls."""
+    import torch
+    import paper_1309_1894_gb300 as wx
+    from paper_1309_1894_gb300 import synth
+    n = args.single
+    nvec = {"axpbypcz": 3, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3}[args.vecop]
+    v = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(nvec)]
+    for k, t in enumerate(v):
+        wx.wxpy_fill_uniform(t, synth.BASE_SEED + k, synth.TAG_X)
+    add, mul = (int(t) for t in args.pipes.split(","))
+    wx.wxpy_vecops_pipes(add, mul)
+    for _ in range(args.reps):
+        if args.vecop == "axpbypcz":
+            wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])
+        elif args.vecop == "pointwise_mult":
+            wx.wxpy_pointwise_mult(v[0], v[1], v[2])
+        else:
+            m = nvec - 1
+            wx.wxpy_maxpy([0.25 * (j + 1) for j in range(m)], v[1:], v[0])
+    torch.cuda.synchronize()
+    wx.wxpy_vecops_status()
+    print(json.dumps({"vecop": args.vecop, "n": n, "reps": args.reps, "pipes": [add, mul]}),
+          flush=True)
     return 0
 
 

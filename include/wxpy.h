@@ -237,13 +237,52 @@ int wxpy_pointwise_mult(int64_t n, const double *x, const double *y, double *w, 
  * rounded integer-pipeline operations instead of FP64 instructions.
  * add_offload: the sums (0 none, 1 every other one, 2 all); mul_sixteenths:
  * the fraction, in sixteenths, of each warp's loop iterations whose products
- * run there (0..16).  -1 in either restores that operation's default (sums
- * in FP64; products 14/16 for axpbypcz, 13/16 for maxpy groups of 2 terms,
+ * run there (0..16).  -1 in either leaves that part to the operation's
+ * searched split (wxpy_vecops_tune) or, when it has none, its default (sums
+ * in FP64; products 14/16 for axpbypcz and for maxpy groups of 2 terms,
  * 16/16 for groups of 3..8, 4/16 for pointwise_mult; a maxpy group of one
- * term runs as wxpy() and its tuned variant).  The bits of every
- * result are the same under every split; only the speed differs.  Process-
- * wide, read at each call.  Errors: WXPY_EINVAL out of range. */
+ * term runs as wxpy() and its tuned variant).  The bits of every result are
+ * the same under every split; only the speed differs.  Process-wide, read at
+ * each call.  Errors: WXPY_EINVAL out of range. */
 int wxpy_vecops_pipes(int add_offload, int mul_sixteenths);
+
+/* The empirical search of Sec. 2 applied to the pipe split of the streaming
+ * sibling kernels.  Classes: */
+#define WXPY_VEC_AXPBYPCZ 0 /* axpbypcz */
+/* 1 .. 7: a maxpy launch group of (class + 1) terms, 2 .. 8 */
+#define WXPY_VEC_PMULT 8    /* pointwise_mult */
+#define WXPY_VEC_CLASSES 9
+
+typedef struct wxpy_vecops_tune_result {
+    int32_t op_class;       /* WXPY_VEC_* */
+    int32_t add_offload;    /* the winning split */
+    int32_t mul_sixteenths;
+    int32_t candidates;     /* splits timed */
+    int32_t rejected;       /* splits whose output differed from the all-FP64 split's */
+    int32_t reserved;
+    double best_us;         /* median device time of the winner, L2 flushed */
+    double default_us;      /* the built-in default split, same conditions */
+    double gbs;             /* algorithmic bytes / best_us */
+} wxpy_vecops_tune_result;
+
+/* For each class, on generator inputs of n elements per vector: the all-FP64
+ * split's output is the reference result; every candidate split (products:
+ * 0, 2, .., 16 sixteenths with the sums in FP64; then the sums every other or
+ * all in the integer pipeline at the best product share) is run once from
+ * pristine inputs and compared with it bit for bit -- a single differing bit
+ * rejects it -- and timed as the median of five runs, each after an L2 flush.
+ * The fastest verified split becomes the class's split for later calls that
+ * leave wxpy_vecops_pipes at -1, and is saved and loaded with the tune cache
+ * (wxpy_tune_cache_save / _load).  `results` (WXPY_VEC_CLASSES entries) may
+ * be NULL.  Allocates about 11 n doubles of scratch while it runs, on the
+ * current device.  Errors: WXPY_EINVAL (n <= 0), WXPY_ENOMEM, WXPY_ECUDA,
+ * WXPY_EMISMATCH (every candidate of a class rejected). */
+int wxpy_vecops_tune(int64_t n, wxpy_vecops_tune_result *results);
+
+/* The searched split of a class (-1, -1 when not searched); set installs one
+ * (add 0..2, mul 0..16) or clears it (-1, -1). */
+int wxpy_vecops_tuned_get(int op_class, int *add_offload, int *mul_sixteenths);
+int wxpy_vecops_tuned_set(int op_class, int add_offload, int mul_sixteenths);
 
 /* axpbypcz, maxpy and pointwise_mult on 32-byte co-aligned pointers stream
  * their inputs into shared memory with bulk asynchronous copies, completed on
@@ -383,7 +422,8 @@ typedef struct wxpy_tune_result {
 int wxpy_tune(int64_t n, unsigned flags, wxpy_tune_result *out);
 
 /* The tuning table: one variant id per cell (tune_key of wxpy_class_info),
- * -1 for an untuned cell.  get/set/clear touch no device. */
+ * -1 for an untuned cell.  get/set/clear touch no device; clear also drops
+ * the searched splits of the sibling kernels (wxpy_vecops_tune). */
 int wxpy_tune_get(int tune_key, int *variant_id);
 int wxpy_tune_set(int tune_key, int variant_id);
 int wxpy_tune_clear(void);

@@ -10,7 +10,11 @@ does not load the library; the first call does, and raises if it is missing.
 from .binding import (  # noqa: F401
     WxpyError, lib, check, version, strerror,
     wxpy, wxpy_host, wxpy_host_config, wxpy_run_variant,
-    wxpy_axpy, wxpy_aypx, wxpy_axpbypcz, wxpy_maxpy, wxpy_pointwise_mult, wxpy_vecops_pipes, wxpy_vecops_status, wxpy_debug_vecops_drop_tile, wxpy_reference, wxpy_lookup, wxpy_classify,
+    wxpy_axpy, wxpy_aypx, wxpy_axpbypcz, wxpy_maxpy, wxpy_pointwise_mult,
+    wxpy_vecops_pipes, wxpy_vecops_status, wxpy_vecops_tune, wxpy_vecops_tuned_get,
+    wxpy_vecops_tuned_set, wxpy_debug_vecops_drop_tile,
+    VEC_AXPBYPCZ, VEC_PMULT, VEC_CLASSES, VEC_CLASS_NAMES,
+    wxpy_reference, wxpy_lookup, wxpy_classify,
     wxpy_device_query, wxpy_variant_count, wxpy_variant_describe, wxpy_variant_encode,
     wxpy_set_variant, wxpy_debug_inject_launch_error, wxpy_fill_uniform,
     wxpy_tune, wxpy_tune_get, wxpy_tune_set, wxpy_tune_clear, wxpy_tune_cache_save,

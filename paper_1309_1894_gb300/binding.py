@@ -72,6 +72,23 @@ class TuneResult(ctypes.Structure):
 
 TUNE_ALIGN16, TUNE_ALIGN8, TUNE_XY, TUNE_WALIAS, TUNE_QUICK, TUNE_RESIDENT = 1, 2, 4, 8, 16, 32
 
+# sibling-kernel classes of the pipe-split search (1 .. 7: maxpy groups of 2 .. 8 terms)
+VEC_AXPBYPCZ, VEC_PMULT, VEC_CLASSES = 0, 8, 9
+VEC_CLASS_NAMES = ["axpbypcz"] + [f"maxpy{m}" for m in range(2, 9)] + ["pointwise_mult"]
+
+
+class VecopsTuneResult(ctypes.Structure):
+    _fields_ = [("op_class", ctypes.c_int32), ("add_offload", ctypes.c_int32),
+                ("mul_sixteenths", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("rejected", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("best_us", ctypes.c_double), ("default_us", ctypes.c_double),
+                ("gbs", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["op"] = VEC_CLASS_NAMES[self.op_class]
+        return d
+
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -120,6 +137,9 @@ SIGNATURES = {
     "wxpy_pointwise_mult": (_INT, [_I64, _P, _P, _P, _P]),
     "wxpy_vecops_pipes": (_INT, [_INT, _INT]),
     "wxpy_vecops_status": (_INT, []),
+    "wxpy_vecops_tune": (_INT, [_I64, ctypes.POINTER(VecopsTuneResult)]),
+    "wxpy_vecops_tuned_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    "wxpy_vecops_tuned_set": (_INT, [_INT, _INT, _INT]),
     "wxpy_debug_vecops_drop_tile": (_INT, [_I64]),
     "wxpy_host": (_INT, [_I64, _D, _P, _P, _P, _P]),
     "wxpy_host_config": (_INT, [_I64, _INT, _INT]),
@@ -334,6 +354,25 @@ def wxpy_pointwise_mult(x, y, w=None, stream=None):
 def wxpy_vecops_pipes(add_offload: int = -1, mul_sixteenths: int = -1) -> None:
     """Pipe split of axpbypcz / maxpy / pointwise_mult (-1: the operation's default)."""
     check(lib().wxpy_vecops_pipes(add_offload, mul_sixteenths), "wxpy_vecops_pipes")
+
+
+def wxpy_vecops_tune(n: int) -> list[dict]:
+    """The pipe-split search of every sibling-kernel class on n-element vectors."""
+    res = (VecopsTuneResult * VEC_CLASSES)()
+    check(lib().wxpy_vecops_tune(n, res), "wxpy_vecops_tune")
+    return [r.as_dict() for r in res]
+
+
+def wxpy_vecops_tuned_get(op_class: int) -> tuple[int, int]:
+    a, m = _INT(), _INT()
+    check(lib().wxpy_vecops_tuned_get(op_class, ctypes.byref(a), ctypes.byref(m)),
+          "wxpy_vecops_tuned_get")
+    return a.value, m.value
+
+
+def wxpy_vecops_tuned_set(op_class: int, add_offload: int, mul_sixteenths: int) -> None:
+    check(lib().wxpy_vecops_tuned_set(op_class, add_offload, mul_sixteenths),
+          "wxpy_vecops_tuned_set")
 
 
 def wxpy_vecops_status() -> None:

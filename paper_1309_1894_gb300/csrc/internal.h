@@ -118,6 +118,20 @@ int launch_count_mismatch(const double *a, const double *b, int64_t n,
                           unsigned long long *count_dev, cudaStream_t s);
 int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s);
 
+// vecops.cu: the sibling kernels by class (WXPY_VEC_*), under an explicit
+// pipe split, and the table of searched splits.
+struct VecPipes {
+    int add, mul;  // add offload 0..2, product sixteenths 0..16
+};
+// Classes: axpbypcz in = {x, y, z}, out = z; maxpy with m = class + 1 terms
+// in = {y, x0 .. x_{m-1}}, out = y; pointwise_mult in = {x, y}, out separate.
+int vecops_inputs(int cls);
+int vecops_run(int cls, int64_t n, const double *coef, const double *const *in, double *out,
+               VecPipes p, cudaStream_t s);
+VecPipes vecops_default(int cls);
+bool vecops_tuned_load(int cls, VecPipes *p);
+void vecops_tuned_store(int cls, const VecPipes *p);  // nullptr clears
+
 cudaError_t launch_reference(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s);
 SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy);
 

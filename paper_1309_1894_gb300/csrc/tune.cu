@@ -354,6 +354,21 @@ int cache_save(const char *path) {
         }
         out += "\n  ],";
     }
+    {
+        out += "\n  \"vecops\": [";
+        bool vfirst = true;
+        for (int c = 0; c < WXPY_VEC_CLASSES; ++c) {
+            VecPipes vp;
+            if (!vecops_tuned_load(c, &vp)) continue;
+            char buf[120];
+            std::snprintf(buf, sizeof buf,
+                          "%s\n    {\"class\": %d, \"add_offload\": %d, \"mul_sixteenths\": %d}",
+                          vfirst ? "" : ",", c, vp.add, vp.mul);
+            out += buf;
+            vfirst = false;
+        }
+        out += "\n  ],";
+    }
     out += "\n  \"entries\": [";
     bool first = true;
     for (int k = 0; k < kTuneKeys; ++k) {
@@ -451,8 +466,27 @@ int cache_load(const char *path, const char *expect_device) {
             }
         }
     }
+    // Optional searched splits of the sibling kernels.
+    std::vector<std::pair<int, VecPipes>> vec;
+    size_t vpos = s.find("\"vecops\"");
+    if (vpos != std::string::npos) {
+        const size_t vend = s.find(']', vpos);
+        if (vend == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated vecops", path);
+        size_t q = vpos;
+        while ((q = s.find('{', q + 1)) != std::string::npos && q < vend) {
+            const size_t r = s.find('}', q);
+            long long c = -1, a = -1, m = -1;
+            if (r == std::string::npos || !find_int(s, q, r, "class", &c) ||
+                !find_int(s, q, r, "add_offload", &a) || !find_int(s, q, r, "mul_sixteenths", &m) ||
+                c < 0 || c >= WXPY_VEC_CLASSES || a < 0 || a > 2 || m < 0 || m > 16)
+                return fail(WXPY_EINVAL, "%s: malformed vecops entry", path);
+            vec.push_back({(int)c, VecPipes{(int)a, (int)m}});
+            q = r;
+        }
+    }
     for (auto &kv : entries) g_tuned[kv.first].store(kv.second);
     if (have_batch) set_batch_shape(bs);
+    for (auto &cv : vec) vecops_tuned_store(cv.first, &cv.second);
     return WXPY_OK;
 }
 
@@ -507,6 +541,7 @@ int wxpy_tune_set(int tune_key, int variant_id) {
 
 int wxpy_tune_clear(void) {
     for (auto &t : g_tuned) t.store(-1);
+    for (int c = 0; c < WXPY_VEC_CLASSES; ++c) vecops_tuned_store(c, nullptr);
     return WXPY_OK;
 }
 

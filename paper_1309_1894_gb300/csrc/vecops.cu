@@ -21,13 +21,13 @@
 // has 3 products and 2 sums per element (32 bytes of traffic), maxpy with m
 // terms 2m operations per 8(m + 2) bytes.  Both are FP64-bound far below the
 // HBM roofline unless part of the arithmetic moves to the integer pipelines
-// (fp64_emu.cuh).  A product costs about forty ALU operations there and a sum
-// about seventy-five, so products are the cheaper ones to move: a runtime
-// fraction (in sixteenths) of each warp's loop iterations computes all of
-// its products in the integer pipeline, the rest in FP64; the choice is
-// uniform across the warp (no divergence) and rotates with the iteration, so
-// every SM sub-partition sees the same mix.  Sums can move too (add offload
-// 1: every other one, 2: all).  Every split gives the same bits.
+// (fp64_emu.cuh, fp64_mul.cuh).  A product costs about thirty ALU operations
+// there and a sum about seventy-five, so products are the cheaper ones to
+// move: a runtime fraction (in sixteenths) of each warp's loop iterations
+// computes all of its products in the integer pipeline, the rest in FP64;
+// the choice is uniform across the warp (no divergence) and rotates with the
+// iteration, so every SM sub-partition sees the same mix.  Sums can move too
+// (add offload 1: every other one, 2: all).  Every split gives the same bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +35,7 @@
 #include <cstring>
 
 #include "bulk.cuh"
+#include "fp64_mul.cuh"
 #include "internal.h"
 
 namespace wx {
@@ -268,6 +269,9 @@ struct StageShape {
     static constexpr int kTileBytes = NIN * kTile * 8;
     static constexpr int kStages = std::max(2, std::min(4, (72 * 1024) / kTileBytes));
     static constexpr int kSmem = kStages * kTileBytes;
+    // three resident blocks for the widest maxpy groups (a register cap of 75
+    // measured 6 % faster there; narrower operations gain nothing from it)
+    static constexpr int kMinBlocks = NIN >= 7 ? 3 : 2;
 };
 
 __device__ __forceinline__ void ld_shared_v2(const double *p, double &a, double &b) {
@@ -303,7 +307,8 @@ __device__ __forceinline__ void staged_tile(const Coefs &cf, const double *sb, d
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kStagedThreads, 2) ew_staged_kernel(const EwArgs<Op::kIn> a) {
+__global__ void __launch_bounds__(kStagedThreads, StageShape<Op::kIn>::kMinBlocks)
+    ew_staged_kernel(const EwArgs<Op::kIn> a) {
     constexpr int NIN = Op::kIn;
     using SS = StageShape<NIN>;
     constexpr int TE = SS::kTile, S = SS::kStages;
@@ -475,39 +480,82 @@ int launch_ew(const double *const *in, double *out, int64_t n, const double *coe
 }
 
 // Pipe split: add offload (0, 1, 2) and product sixteenths (0..16); -1 in
-// either leaves the operation's own default (below).
+// either leaves the operation's searched split, else its default (below).
 std::atomic<int> g_vec_add{-1};
 std::atomic<int> g_vec_mul{-1};
+std::atomic<int> g_vec_tuned[WXPY_VEC_CLASSES] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 
-struct Pipes {
-    int add, mul;
-};
+using Pipes = VecPipes;
 
-Pipes pipes_or(Pipes dflt) {
+Pipes pipes_for(int cls) {
+    Pipes p = vecops_default(cls);
+    vecops_tuned_load(cls, &p);
     const int add = g_vec_add.load(), mul = g_vec_mul.load();
-    return {add < 0 ? dflt.add : add, mul < 0 ? dflt.mul : mul};
+    if (add >= 0) p.add = add;
+    if (mul >= 0) p.mul = mul;
+    return p;
 }
 
-// Defaults, measured on GB300 at n = 2^26 (sums in FP64, the cheaper pipe for
-// them; the product share that balances the FP64 and ALU pipelines).
-Pipes default_axpbypcz() { return {0, 14}; }
-Pipes default_maxpy(int m) { return {0, m == 2 ? 13 : 16}; }
-constexpr int kDefaultPmultMul = 4;
-
 template <int M>
-int maxpy_group(int64_t n, const double *alpha, const double *const *x, double *y, cudaStream_t s) {
-    const double *in[M + 1];
-    in[0] = y;
-    for (int j = 0; j < M; ++j) in[j + 1] = x[j];
-    const Pipes p = pipes_or(default_maxpy(M));
+int maxpy_group(int64_t n, const double *alpha, const double *const *in, Pipes p, cudaStream_t s) {
     switch (p.add) {
-        case 0: return launch_ew<MaxpyOp<M, 0>>(in, y, n, alpha, M, p.mul, s);
-        case 1: return launch_ew<MaxpyOp<M, 1>>(in, y, n, alpha, M, p.mul, s);
-        default: return launch_ew<MaxpyOp<M, 2>>(in, y, n, alpha, M, p.mul, s);
+        case 0: return launch_ew<MaxpyOp<M, 0>>(in, (double *)in[0], n, alpha, M, p.mul, s);
+        case 1: return launch_ew<MaxpyOp<M, 1>>(in, (double *)in[0], n, alpha, M, p.mul, s);
+        default: return launch_ew<MaxpyOp<M, 2>>(in, (double *)in[0], n, alpha, M, p.mul, s);
     }
 }
 
 }  // namespace
+
+// Defaults, measured on GB300 at n = 2^26 (sums in FP64, the cheaper pipe for
+// them; the product share that balanced the FP64 and ALU pipelines best).
+VecPipes vecops_default(int cls) {
+    if (cls == WXPY_VEC_AXPBYPCZ) return {0, 14};
+    if (cls == WXPY_VEC_PMULT) return {0, 4};
+    return {0, cls + 1 == 2 ? 14 : 16};  // maxpy with cls + 1 terms
+}
+
+int vecops_inputs(int cls) {
+    if (cls == WXPY_VEC_AXPBYPCZ) return 3;
+    if (cls == WXPY_VEC_PMULT) return 2;
+    return cls + 2;  // y and cls + 1 x vectors
+}
+
+bool vecops_tuned_load(int cls, VecPipes *p) {
+    if (cls < 0 || cls >= WXPY_VEC_CLASSES) return false;
+    const int v = g_vec_tuned[cls].load();
+    if (v < 0) return false;
+    p->add = v >> 5;
+    p->mul = v & 31;
+    return true;
+}
+
+void vecops_tuned_store(int cls, const VecPipes *p) {
+    if (cls < 0 || cls >= WXPY_VEC_CLASSES) return;
+    g_vec_tuned[cls].store(p ? (p->add << 5) | p->mul : -1);
+}
+
+int vecops_run(int cls, int64_t n, const double *coef, const double *const *in, double *out,
+               VecPipes p, cudaStream_t s) {
+    switch (cls) {
+        case WXPY_VEC_AXPBYPCZ:
+            switch (p.add) {
+                case 0: return launch_ew<AxpbypczOp<0>>(in, out, n, coef, 3, p.mul, s);
+                case 1: return launch_ew<AxpbypczOp<1>>(in, out, n, coef, 3, p.mul, s);
+                default: return launch_ew<AxpbypczOp<2>>(in, out, n, coef, 3, p.mul, s);
+            }
+        case WXPY_VEC_PMULT: return launch_ew<PmultOp>(in, out, n, nullptr, 0, p.mul, s);
+        case 1: return maxpy_group<2>(n, coef, in, p, s);
+        case 2: return maxpy_group<3>(n, coef, in, p, s);
+        case 3: return maxpy_group<4>(n, coef, in, p, s);
+        case 4: return maxpy_group<5>(n, coef, in, p, s);
+        case 5: return maxpy_group<6>(n, coef, in, p, s);
+        case 6: return maxpy_group<7>(n, coef, in, p, s);
+        case 7: return maxpy_group<8>(n, coef, in, p, s);
+        default: return fail(WXPY_EINVAL, "bad vector kernel class %d", cls);
+    }
+}
+
 }  // namespace wx
 
 using namespace wx;
@@ -526,13 +574,8 @@ int wxpy_axpbypcz(int64_t n, double alpha, double beta, double gamma, const doub
                   const double *y, double *z, void *stream) {
     const double *in[3] = {x, y, z};
     const double coef[3] = {alpha, beta, gamma};
-    cudaStream_t s = (cudaStream_t)stream;
-    const Pipes p = pipes_or(default_axpbypcz());
-    switch (p.add) {
-        case 0: return launch_ew<AxpbypczOp<0>>(in, z, n, coef, 3, p.mul, s);
-        case 1: return launch_ew<AxpbypczOp<1>>(in, z, n, coef, 3, p.mul, s);
-        default: return launch_ew<AxpbypczOp<2>>(in, z, n, coef, 3, p.mul, s);
-    }
+    return vecops_run(WXPY_VEC_AXPBYPCZ, n, coef, in, z, pipes_for(WXPY_VEC_AXPBYPCZ),
+                      (cudaStream_t)stream);
 }
 
 int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, double *y,
@@ -549,16 +592,14 @@ int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, do
     for (int j0 = 0; j0 < m; j0 += 8) {
         const int g = std::min(8, m - j0);
         int st;
-        switch (g) {
+        if (g == 1) {
             // a single term is y = RN(y + RN(a x)) = RN(RN(a x) + y): wxpy into y
-            case 1: st = wxpy(n, alpha[j0], x[j0], y, y, stream); break;
-            case 2: st = maxpy_group<2>(n, alpha + j0, x + j0, y, s); break;
-            case 3: st = maxpy_group<3>(n, alpha + j0, x + j0, y, s); break;
-            case 4: st = maxpy_group<4>(n, alpha + j0, x + j0, y, s); break;
-            case 5: st = maxpy_group<5>(n, alpha + j0, x + j0, y, s); break;
-            case 6: st = maxpy_group<6>(n, alpha + j0, x + j0, y, s); break;
-            case 7: st = maxpy_group<7>(n, alpha + j0, x + j0, y, s); break;
-            default: st = maxpy_group<8>(n, alpha + j0, x + j0, y, s); break;
+            st = wxpy(n, alpha[j0], x[j0], y, y, stream);
+        } else {
+            const double *in[9];
+            in[0] = y;
+            for (int j = 0; j < g; ++j) in[j + 1] = x[j0 + j];
+            st = vecops_run(g - 1, n, alpha + j0, in, y, pipes_for(g - 1), s);
         }
         if (st != WXPY_OK) return st;
     }
@@ -567,11 +608,8 @@ int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, do
 
 int wxpy_pointwise_mult(int64_t n, const double *x, const double *y, double *w, void *stream) {
     const double *in[2] = {x, y};
-    // One product per 24 bytes leaves FP64 below its ceiling; a small share
-    // in the integer pipeline still measured a few percent faster.
-    const int mul = g_vec_mul.load();
-    return launch_ew<PmultOp>(in, w, n, nullptr, 0, mul < 0 ? kDefaultPmultMul : mul,
-                              (cudaStream_t)stream);
+    return vecops_run(WXPY_VEC_PMULT, n, nullptr, in, w, pipes_for(WXPY_VEC_PMULT),
+                      (cudaStream_t)stream);
 }
 
 int wxpy_vecops_pipes(int add_offload, int mul_sixteenths) {

@@ -227,3 +227,40 @@ def test_full_size_sampled():
     assert np.array_equal(vs[2][pos].cpu().numpy().view(np.uint64), z_want.view(np.uint64))
     y_want = oracle.maxpy(al, [host[0], host[1], z_want, host[4]], host[3])
     assert np.array_equal(vs[3][pos].cpu().numpy().view(np.uint64), y_want.view(np.uint64))
+
+
+def test_pipe_split_search_then_parity(tmp_path):
+    """Sec. 2 applied to the pipe split: every candidate verified bitwise
+    against the all-FP64 split, none rejected, each winner installed and used;
+    the results survive a tune-cache round trip."""
+    try:
+        res = wx.wxpy_vecops_tune(1 << 20)
+        assert [r["op_class"] for r in res] == list(range(wx.VEC_CLASSES))
+        for r in res:
+            assert r["rejected"] == 0, r
+            assert r["candidates"] == (9 if r["op_class"] == wx.VEC_PMULT else 11), r
+            assert 0 < r["best_us"] <= r["default_us"] * 1.5, r
+            assert wx.wxpy_vecops_tuned_get(r["op_class"]) == (r["add_offload"], r["mul_sixteenths"])
+        n = 100003
+        xh, yh, zh = (vals(700 + k, n, True) for k in range(3))
+        gx, gy, gz = Guarded(n, 8).set(xh), Guarded(n, 8).set(yh), Guarded(n, 8).set(zh)
+        wx.wxpy_axpbypcz(1.5, -0.5, 0.25, gx.t, gy.t, gz.t)
+        torch.cuda.synchronize()
+        assert same(gz.t, oracle.axpbypcz(1.5, -0.5, 0.25, xh, yh, zh))
+        xs = [vals(800 + j, n, False) for j in range(5)]
+        gxs = [Guarded(n, 8).set(x) for x in xs]
+        gy.set(yh)
+        al = [0.5, -1.0, 1.5, -2.0, 0.25]
+        wx.wxpy_maxpy(al, [g.t for g in gxs], gy.t)
+        torch.cuda.synchronize()
+        assert same(gy.t, oracle.maxpy(al, xs, yh))
+        path = str(tmp_path / "tune.json")
+        wx.wxpy_tune_cache_save(path)
+        wx.wxpy_tune_clear()
+        assert wx.wxpy_vecops_tuned_get(0) == (-1, -1)
+        wx.wxpy_tune_cache_load(path, check_device=True)
+        for r in res:
+            assert wx.wxpy_vecops_tuned_get(r["op_class"]) == (r["add_offload"], r["mul_sixteenths"])
+    finally:
+        for c in range(wx.VEC_CLASSES):
+            wx.wxpy_vecops_tuned_set(c, -1, -1)

@@ -60,3 +60,49 @@ def test_missing_file(tmp_path):
     with pytest.raises(wx.WxpyError) as e:
         wx.wxpy_tune_cache_load(str(tmp_path / "nope.json"), check_device=False)
     assert e.value.status == wx.WXPY_ENOTFOUND
+
+
+def test_vecops_split_set_get_clear():
+    assert wx.wxpy_vecops_tuned_get(wx.VEC_AXPBYPCZ) == (-1, -1)
+    wx.wxpy_vecops_tuned_set(wx.VEC_AXPBYPCZ, 0, 12)
+    assert wx.wxpy_vecops_tuned_get(wx.VEC_AXPBYPCZ) == (0, 12)
+    wx.wxpy_vecops_tuned_set(wx.VEC_AXPBYPCZ, -1, -1)
+    assert wx.wxpy_vecops_tuned_get(wx.VEC_AXPBYPCZ) == (-1, -1)
+    wx.wxpy_vecops_tuned_set(3, 2, 16)
+    wx.wxpy_tune_clear()  # drops the searched splits too
+    assert wx.wxpy_vecops_tuned_get(3) == (-1, -1)
+    for bad in ((wx.VEC_CLASSES, 0, 4), (-1, 0, 4), (0, 3, 4), (0, 0, 17), (0, -1, 4),
+                (wx.VEC_PMULT, 1, 4)):  # pointwise_mult has no sums to offload
+        with pytest.raises(wx.WxpyError) as e:
+            wx.wxpy_vecops_tuned_set(*bad)
+        assert e.value.status == wx.WXPY_EINVAL
+
+
+def test_load_vecops_section(tmp_path):
+    path = tmp_path / "v.json"
+    path.write_text(json.dumps({"format": "wxpy-tune-1", "device": "X",
+                                "vecops": [{"class": 3, "add_offload": 1, "mul_sixteenths": 10},
+                                           {"class": 8, "add_offload": 0, "mul_sixteenths": 2}],
+                                "entries": [{"key": 4, "variant": 11}]}))
+    wx.wxpy_tune_cache_load(str(path), check_device=False)
+    assert wx.wxpy_vecops_tuned_get(3) == (1, 10)
+    assert wx.wxpy_vecops_tuned_get(8) == (0, 2)
+    assert wx.wxpy_vecops_tuned_get(0) == (-1, -1)
+    assert wx.wxpy_tune_get(4) == 11
+
+
+@pytest.mark.parametrize("entry", [{"class": 9, "add_offload": 0, "mul_sixteenths": 2},
+                                   {"class": 1, "add_offload": 3, "mul_sixteenths": 2},
+                                   {"class": 1, "add_offload": 0, "mul_sixteenths": 17},
+                                   {"class": 1, "add_offload": 0}])
+def test_malformed_vecops_entry_stores_nothing(tmp_path, entry):
+    path = tmp_path / "bad.json"
+    path.write_text(json.dumps({"format": "wxpy-tune-1", "device": "X",
+                                "vecops": [{"class": 2, "add_offload": 0, "mul_sixteenths": 6},
+                                           entry],
+                                "entries": [{"key": 1, "variant": 2}]}))
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy_tune_cache_load(str(path), check_device=False)
+    assert e.value.status == wx.WXPY_EINVAL
+    assert wx.wxpy_vecops_tuned_get(2) == (-1, -1)
+    assert wx.wxpy_tune_get(1) == -1

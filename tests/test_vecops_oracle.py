@@ -96,6 +96,14 @@ def check_closed_forms(L):
     if not np.array_equal(oracle.pmult(x, np.ones_like(x), library=L).view(np.uint64),
                           x.view(np.uint64)):
         return "pmult by 1"
+    # maxpy is m successive axpy calls (the left-to-right reading, y the running sum)
+    al = [0.5, -3.0, 1.0 + 2.0 ** -52]
+    xs = [x, z, np.ldexp(y, -3)]
+    acc = y
+    for a_j, x_j in zip(al, xs):
+        acc = oracle.axpy(a_j, x_j, acc, library=L)
+    if not np.array_equal(oracle.maxpy(al, xs, y, library=L).view(np.uint64), acc.view(np.uint64)):
+        return "maxpy vs successive axpy"
     # axpy agrees with the wxpy oracle (two independent implementations)
     if not np.array_equal(oracle.axpy(0.75, x, y, library=L).view(np.uint64),
                           oracle.wxpy(0.75, x, y).view(np.uint64)):
@@ -119,6 +127,9 @@ MUTANTS = {
     "aypx_swapped": ("double prod = alpha * y[i];\n        double sum = x[i] + prod;",
                      "double prod = alpha * x[i];\n        double sum = y[i] + prod;"),
     "pmult_square": ("double prod = x[i] * y[i];", "double prod = x[i] * x[i];"),
+    "maxpy_alpha0": ("double prod = alpha[j] * x[j][i];", "double prod = alpha[0] * x[j][i];"),
+    "maxpy_drops_last": ("        for (j = 0; j < m; ++j) {\n            double prod",
+                         "        for (j = 0; j + 1 < m; ++j) {\n            double prod"),
 }
 
 
