@@ -406,6 +406,7 @@ def run_ours(args):
         result["vecops"] = measure_vecops(wx, torch, dev, stream, peak)
         if args.serve_seconds > 0:
             result["served"] = measure_served(args.serve_seconds)
+        result["cpu_family"] = measure_cpu_family()
     if rank == 0:
         rate1, passes, dt = cpu_oracle_rate(24, args.cpu_seconds, threads=1)
         cores = host_cores()
@@ -709,6 +710,35 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
                        "classes": [{k: r[k] for k in ("op", "add_offload", "mul_sixteenths",
                                                      "candidates", "rejected", "best_us",
                                                      "default_us", "gbs")} for r in search]}}
+
+
+def measure_cpu_family():
+    """The paper's own experiment on the host cores (Sec. 3, Fig. 1): the host
+    VecWXPY family's search against the baseline it reports -- the plain loop
+    at -O3, vectorised by the compiler alone, one thread -- at an in-cache
+    size (n = 2^14, 384 KiB, warm) and a DRAM size (n = 2^24, 384 MiB, cache
+    flushed).  GB/s of algorithmic bytes (24 per element), from the search's
+    median times."""
+    from paper_1309_1894_gb300 import build as wbuild
+    from paper_1309_1894_gb300 import cpu_family as cf
+    wbuild.build_cpu()
+    out = {"baseline_variant": cf.describe(cf.baseline_variant()), "sizes": []}
+    for n, warm in ((1 << 14, True), (1 << 24, False)):
+        t0 = time.time()
+        res = cf.tune(n, warm=warm)
+        secs = time.time() - t0
+        gbs = lambda us: 24 * n / (us * 1e3)
+        out["sizes"].append({
+            "n": n, "warm": warm, "search_seconds": secs, "candidates": res["candidates"],
+            "rejected": res["rejected"],
+            "baseline_gbs": gbs(res["baseline_us"]),
+            "reference_o2_novec_gbs": gbs(res["reference_us"]),
+            "best_one_thread": {"variant": res["best_single_variant"],
+                                "gbs": gbs(res["best_single_us"]),
+                                "speedup_vs_baseline": res["baseline_us"] / res["best_single_us"]},
+            "best": {"variant": res["best_variant"], "gbs": gbs(res["best_us"]),
+                     "speedup_vs_baseline": res["baseline_us"] / res["best_us"]}})
+    return out
 
 
 SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)

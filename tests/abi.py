@@ -6,10 +6,10 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions() -> list[str]:
-    """Names of the functions declared in include/*.h (comments stripped)."""
+def declared_functions(header: str = "wxpy.h") -> list[str]:
+    """Names of the functions declared in include/<header> (comments stripped)."""
     names = []
-    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+    for path in [os.path.join(ROOT, "include", header)]:
         with open(path) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
