@@ -715,15 +715,15 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
 def measure_cpu_family():
     """The paper's own experiment on the host cores (Sec. 3, Fig. 1): the host
     VecWXPY family's search against the baseline it reports -- the plain loop
-    at -O3, vectorised by the compiler alone, one thread -- at an in-cache
-    size (n = 2^14, 384 KiB, warm) and a DRAM size (n = 2^24, 384 MiB, cache
-    flushed).  GB/s of algorithmic bytes (24 per element), from the search's
-    median times."""
+    at -O3, vectorised by the compiler alone, one thread -- per vector size
+    as in the paper's figure: n = 2^10 .. 2^20 warm (cache-resident inputs)
+    and n = 2^24 (384 MiB, cache flushed).  GB/s of algorithmic bytes (24 per
+    element), from the search's median times."""
     from paper_1309_1894_gb300 import build as wbuild
     from paper_1309_1894_gb300 import cpu_family as cf
     wbuild.build_cpu()
     out = {"baseline_variant": cf.describe(cf.baseline_variant()), "sizes": []}
-    for n, warm in ((1 << 14, True), (1 << 24, False)):
+    for n, warm in [(1 << k, True) for k in (10, 12, 14, 16, 18, 20)] + [(1 << 24, False)]:
         t0 = time.time()
         res = cf.tune(n, warm=warm)
         secs = time.time() - t0

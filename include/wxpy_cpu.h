@@ -14,7 +14,7 @@
  * Variants.  A variant is (flavour, kernel, threads):
  *   - flavour: the compiler flags the kernels were built with (0: -O2
  *     -fno-tree-vectorize; 1: -O3; 2: -O3 plus this machine's CPU target,
- *     e.g. -mcpu=neoverse-v2 on Grace), every one with -ffp-contract=off;
+ *     e.g. -mcpu=neoverse-v2+nosve on Grace), every one with -ffp-contract=off;
  *   - kernel: 0 the plain loop (vectorised by the compiler alone), 1 .. 12
  *     explicit SIMD, VW = 1, 2, 4, 8 doubles per vector x U = 1, 2, 4 vectors
  *     per step;

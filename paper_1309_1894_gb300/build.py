@@ -94,10 +94,12 @@ CPU_COMMON = ["-fPIC", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-Wa
 
 def cpu_flavours() -> list[list[str]]:
     """Flags of flavours 0, 1, 2.  Flavour 2 adds the CPU target of the machine
-    the library is built on (Grace's Neoverse V2 on the GPU machine); elsewhere it
-    adds loop unrolling, and never -march=native."""
+    the library is built on (Grace's Neoverse V2 on the GPU machine, with SVE
+    disabled: the box's kernel does not expose it, so SVE code would trap);
+    elsewhere it adds loop unrolling, and never -march=native."""
     import platform
-    f2 = ["-O3", "-mcpu=neoverse-v2"] if platform.machine() == "aarch64" else ["-O3", "-funroll-loops"]
+    f2 = (["-O3", "-mcpu=neoverse-v2+nosve"] if platform.machine() == "aarch64"
+          else ["-O3", "-funroll-loops"])
     return [["-O2", "-fno-tree-vectorize"], ["-O3"], f2]
 
 
