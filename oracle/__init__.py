@@ -188,6 +188,59 @@ def pmult(x, y, library=None):
     return out
 
 
+REDUCE_SOURCE = os.path.join(HERE, "reduce_oracle.c")
+REDUCE_LIBRARY = os.path.join(HERE, "liboracle_reduce.so")
+REDUCE_TILE = 8192
+_reduce_lib = None
+
+
+def load_reduce_library(path: str) -> ctypes.CDLL:
+    """Load an oracle library built from ``reduce_oracle.c`` (or a copy)."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    L = ctypes.CDLL(path)
+    i64, d = ctypes.c_int64, ctypes.c_double
+    for name, args in (("oracle_wxpy_norm2", [i64, d, dp, dp, dp, dp]),
+                       ("oracle_wxpy_dot", [i64, d, dp, dp, dp, dp, dp])):
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = args
+    return L
+
+
+def reduce_lib() -> ctypes.CDLL:
+    """The update-and-reduce oracle library, built on first use."""
+    global _reduce_lib
+    with _lock:
+        if _reduce_lib is None:
+            _reduce_lib = load_reduce_library(build(source=REDUCE_SOURCE, output=REDUCE_LIBRARY))
+        return _reduce_lib
+
+
+def wxpy_norm2(alpha, x, y, library=None):
+    """(w, s): w = RN(RN(alpha*x) + y) and s = TREE(RN(w*w)) (see reduce_oracle.c)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.empty_like(x)
+    res = np.zeros(1)
+    L = library or reduce_lib()
+    _vcheck(L.oracle_wxpy_norm2(x.shape[0], float(alpha), _dptr(x), _dptr(y), _dptr(w),
+                                _dptr(res)), "oracle_wxpy_norm2")
+    return w, float(res[0])
+
+
+def wxpy_dot(alpha, x, y, z, library=None):
+    """(w, s): w = RN(RN(alpha*x) + y) and s = TREE(RN(w*z)) (see reduce_oracle.c)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = np.empty_like(x)
+    res = np.zeros(1)
+    L = library or reduce_lib()
+    _vcheck(L.oracle_wxpy_dot(x.shape[0], float(alpha), _dptr(x), _dptr(y), _dptr(w), _dptr(z),
+                              _dptr(res)), "oracle_wxpy_dot")
+    return w, float(res[0])
+
+
 def wxpy_batch(alphas, xs, ys, library: ctypes.CDLL | None = None):
     """Batched oracle: one output array per segment (a list)."""
     count = len(xs)
