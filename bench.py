@@ -404,6 +404,7 @@ def run_ours(args):
         result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
         result["batched"] = measure_batched(wx, lib, torch, dev, sh, stream, peak)
         result["vecops"] = measure_vecops(wx, torch, dev, stream, peak)
+        result["reduce"] = measure_reduce(wx, torch, dev, stream, peak)
         if args.serve_seconds > 0:
             result["served"] = measure_served(args.serve_seconds)
         result["cpu_family"] = measure_cpu_family()
@@ -712,6 +713,54 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
                                                      "default_us", "gbs")} for r in search]}}
 
 
+def measure_reduce(wx, torch, dev, stream, peak, reps=10):
+    """The update fused with a reduction of its result, n = 2^26: GB/s of
+    algorithmic bytes (norm2: x, y read and w written, 24 B/element; dot: z
+    read too, 32 B) under each product split (sixteenths of the tiles whose
+    products run in the integer pipelines), and plain wxpy() on the same
+    vectors for the cost
+    of the fused reduction."""
+    n = 1 << 26
+    x, y, z = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
+    for k, t in enumerate((x, y, z)):
+        wx.wxpy_fill_uniform(t, 300 + k, 1)
+    w = torch.empty_like(x)
+    res = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = wx.reduce_workspace(n, dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    norm2 = lambda: wx.wxpy_norm2(-0.625, x, y, w=w, result=res, workspace=ws)
+    dot = lambda: wx.wxpy_dot(-0.625, x, y, z, w=w, result=res, workspace=ws)
+    gbs = lambda nbytes, ms: nbytes / (ms / 1e3) / 1e9
+    splits = []
+    for mul in (0, 4, 8, 12, 16):
+        wx.wxpy_reduce_pipes(mul)
+        splits.append({"mul_sixteenths": mul, "norm2_gbs": gbs(24 * n, timed(norm2)),
+                       "dot_gbs": gbs(32 * n, timed(dot))})
+    wx.wxpy_reduce_pipes(-1)
+    ms_n, ms_d = timed(norm2), timed(dot)
+    ms_w = timed(lambda: wx.wxpy(-0.625, x, y, w))
+    out = {"n": n, "reps": reps,
+           "norm2": {"gbs": gbs(24 * n, ms_n), "frac_of_peak": gbs(24 * n, ms_n) / peak, "ms": ms_n},
+           "dot": {"gbs": gbs(32 * n, ms_d), "frac_of_peak": gbs(32 * n, ms_d) / peak, "ms": ms_d},
+           "wxpy_alone": {"gbs": gbs(24 * n, ms_w), "ms": ms_w},
+           "norm2_time_vs_wxpy": ms_n / ms_w, "splits": splits}
+    del x, y, z, w, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_cpu_family():
     """The paper's own experiment on the host cores (Sec. 3, Fig. 1): the host
     VecWXPY family's search against the baseline it reports -- the plain loop
@@ -829,7 +878,7 @@ def main():
                     help="profiling mode: force this variant id instead of the tuned one")
     ap.add_argument("--vecop", default="",
                     help="profiling mode: only run this sibling kernel (axpbypcz, maxpy4, "
-                         "maxpy8, pointwise_mult) on n = SINGLE, --reps times")
+                         "maxpy8, pointwise_mult, norm2, dot) on n = SINGLE, --reps times")
     ap.add_argument("--pipes", default="-1,-1",
                     help="profiling mode: add offload and product sixteenths for --vecop")
     args = ap.parse_args()
@@ -877,14 +926,23 @@ def run_vecop(args):
     import paper_1309_1894_gb300 as wx
     from paper_1309_1894_gb300 import synth
     n = args.single
-    nvec = {"axpbypcz": 3, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3}[args.vecop]
+    nvec = {"axpbypcz": 3, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3, "norm2": 3,
+            "dot": 4}[args.vecop]
     v = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(nvec)]
     for k, t in enumerate(v):
         wx.wxpy_fill_uniform(t, synth.BASE_SEED + k, synth.TAG_X)
     add, mul = (int(t) for t in args.pipes.split(","))
     wx.wxpy_vecops_pipes(add, mul)
+    if args.vecop in ("norm2", "dot"):
+        ws = wx.reduce_workspace(n)
+        res = torch.empty(1, dtype=torch.float64, device="cuda")
+        wx.wxpy_reduce_pipes(mul)
     for _ in range(args.reps):
-        if args.vecop == "axpbypcz":
+        if args.vecop == "norm2":
+            wx.wxpy_norm2(0.5, v[0], v[1], w=v[2], result=res, workspace=ws)
+        elif args.vecop == "dot":
+            wx.wxpy_dot(0.5, v[0], v[1], v[3], w=v[2], result=res, workspace=ws)
+        elif args.vecop == "axpbypcz":
             wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])
         elif args.vecop == "pointwise_mult":
             wx.wxpy_pointwise_mult(v[0], v[1], v[2])

@@ -292,6 +292,42 @@ int wxpy_vecops_tuned_set(int op_class, int add_offload, int mul_sixteenths);
  * call -- that kernel's output is then incomplete -- else WXPY_OK. */
 int wxpy_vecops_status(void);
 
+/* ---- the update fused with a reduction of its result ---------------------------- */
+
+/* w = RN(RN(alpha*x) + y) (the update of Sec. 3, Fig. 1) and, in the same pass,
+ *   wxpy_norm2: *result = TREE(RN(w[i]*w[i]))        (the squared 2-norm of w)
+ *   wxpy_dot:   *result = TREE(RN(w[i]*z[i]))        (the dot product of w with z)
+ * as a residual update is followed by its norm.  TREE is fixed, so the result
+ * is the same bits on every run and every grid: the indices are cut into
+ * tiles of 8192; a tile's sum is the halving tree e[i] = RN(e[i] + e[i+s]) for
+ * s = 4096, 2048, .., 1 (+0 past n); the tile sums, padded with +0 to a power
+ * of two, are summed by the same tree; n = 0 gives +0.  (The paper defines no
+ * reduction; this one is chosen for reproducibility, and its depth of 13 +
+ * log2(tiles) bounds the rounding error like pairwise summation.)
+ *
+ * Device pointers, asynchronous on `stream`.  x, y, w (and z) as for wxpy():
+ * 8-byte aligned, w either disjoint from or exactly equal to each input (each
+ * element is read before it is written); `result` is one device double,
+ * written when the call completes.  `workspace` is device memory of at least
+ * wxpy_reduce_workspace_bytes(n) bytes, 16-byte aligned, disjoint from the
+ * vectors and result, owned by the caller; the call overwrites it, so calls in
+ * flight at the same time need separate workspaces.  Nothing is allocated.
+ * 32-byte co-aligned pointers take coalesced 32-byte accesses; others element
+ * ones (same bits).  Errors: WXPY_EINVAL (bad argument, workspace too small),
+ * WXPY_EOVERLAP, WXPY_ECUDA. */
+int64_t wxpy_reduce_workspace_bytes(int64_t n);
+int wxpy_norm2(int64_t n, double alpha, const double *x, const double *y, double *w,
+               double *result, void *workspace, int64_t workspace_bytes, void *stream);
+int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *w,
+             const double *z, double *result, void *workspace, int64_t workspace_bytes,
+             void *stream);
+
+/* The share, in sixteenths, of the tiles whose two products per element
+ * (alpha*x and the term) run as the exactly rounded integer-pipeline product
+ * instead of FP64 instructions (a rotation over blocks and tiles): 0..16, -1
+ * the default.  Same bits either way.  Process-wide. */
+int wxpy_reduce_pipes(int mul_sixteenths);
+
 /* ---- batched launch: many independent problems in one launch ----------------- */
 
 /* One problem of a batch: w = RN(RN(alpha*x) + y) over n elements (Sec. 3,

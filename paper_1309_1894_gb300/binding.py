@@ -137,6 +137,10 @@ SIGNATURES = {
     "wxpy_pointwise_mult": (_INT, [_I64, _P, _P, _P, _P]),
     "wxpy_vecops_pipes": (_INT, [_INT, _INT]),
     "wxpy_vecops_status": (_INT, []),
+    "wxpy_reduce_workspace_bytes": (_I64, [_I64]),
+    "wxpy_norm2": (_INT, [_I64, _D, _P, _P, _P, _P, _P, _I64, _P]),
+    "wxpy_dot": (_INT, [_I64, _D, _P, _P, _P, _P, _P, _P, _I64, _P]),
+    "wxpy_reduce_pipes": (_INT, [_INT]),
     "wxpy_vecops_tune": (_INT, [_I64, ctypes.POINTER(VecopsTuneResult)]),
     "wxpy_vecops_tuned_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_vecops_tuned_set": (_INT, [_INT, _INT, _INT]),
@@ -349,6 +353,53 @@ def wxpy_pointwise_mult(x, y, w=None, stream=None):
         raise ValueError("length mismatch")
     check(lib().wxpy_pointwise_mult(n, px, py, pw, _stream_handle(stream)), "wxpy_pointwise_mult")
     return w
+
+
+def reduce_workspace(n: int, device=None):
+    """A workspace tensor (uint8, on the device) for wxpy_norm2 / wxpy_dot of length n."""
+    import torch
+    return torch.empty(max(16, lib().wxpy_reduce_workspace_bytes(n)), dtype=torch.uint8,
+                       device=device or "cuda")
+
+
+def _reduce_args(x, y, w, result, workspace):
+    import torch
+    n, px = _vec(x, "x")
+    ny, py = _vec(y, "y")
+    if w is None:
+        w = torch.empty_like(x)
+    nw, pw = _vec(w, "w")
+    if not (n == ny == nw):
+        raise ValueError("length mismatch")
+    if result is None:
+        result = torch.empty(1, dtype=torch.float64, device=x.device)
+    _, pr = _vec(result, "result")
+    if workspace is None:
+        workspace = reduce_workspace(n, x.device)
+    return n, px, py, w, pw, result, pr, workspace
+
+
+def wxpy_norm2(alpha: float, x, y, w=None, result=None, workspace=None, stream=None):
+    """w <- RN(RN(alpha*x) + y) and result <- the fixed-tree sum of RN(w*w); returns (w, result)."""
+    n, px, py, w, pw, result, pr, ws = _reduce_args(x, y, w, result, workspace)
+    check(lib().wxpy_norm2(n, alpha, px, py, pw, pr, ws.data_ptr(), ws.numel(),
+                           _stream_handle(stream)), "wxpy_norm2")
+    return w, result
+
+
+def wxpy_dot(alpha: float, x, y, z, w=None, result=None, workspace=None, stream=None):
+    """w <- RN(RN(alpha*x) + y) and result <- the fixed-tree sum of RN(w*z); returns (w, result)."""
+    n, px, py, w, pw, result, pr, ws = _reduce_args(x, y, w, result, workspace)
+    nz, pz = _vec(z, "z")
+    if nz != n:
+        raise ValueError("length mismatch")
+    check(lib().wxpy_dot(n, alpha, px, py, pw, pz, pr, ws.data_ptr(), ws.numel(),
+                         _stream_handle(stream)), "wxpy_dot")
+    return w, result
+
+
+def wxpy_reduce_pipes(mul_sixteenths: int = -1) -> None:
+    check(lib().wxpy_reduce_pipes(mul_sixteenths), "wxpy_reduce_pipes")
 
 
 def wxpy_vecops_pipes(add_offload: int = -1, mul_sixteenths: int = -1) -> None:

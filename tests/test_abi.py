@@ -175,3 +175,38 @@ def test_vecops_validation_before_cuda(lib):
     assert lib.wxpy_vecops_pipes(-1, -1) == 0
     assert lib.wxpy_debug_vecops_drop_tile(-2) == wx.WXPY_EINVAL
     assert lib.wxpy_debug_vecops_drop_tile(-1) == 0
+
+
+def test_reduce_validation_before_cuda(lib):
+    ws_need = lib.wxpy_reduce_workspace_bytes(100)
+    assert ws_need == 256 + 8 and lib.wxpy_reduce_workspace_bytes(8193) == 256 + 16
+    assert lib.wxpy_reduce_workspace_bytes(3 * 8192 + 1) == 256 + 8 * 4
+    assert lib.wxpy_reduce_workspace_bytes(-1) == -1
+    X, Y, W, Z, R, WS = (BASE + k * 65536 for k in range(6))
+    args = dict(n=100, x=X, y=Y, w=W, z=Z, r=R, ws=WS, wsb=ws_need)
+
+    def norm2(**kw):
+        a = {**args, **kw}
+        return lib.wxpy_norm2(a["n"], 1.0, a["x"], a["y"], a["w"], a["r"], a["ws"], a["wsb"], None)
+
+    def dot(**kw):
+        a = {**args, **kw}
+        return lib.wxpy_dot(a["n"], 1.0, a["x"], a["y"], a["w"], a["z"], a["r"], a["ws"], a["wsb"],
+                            None)
+
+    for f in (norm2, dot):
+        assert f(n=-1) == wx.WXPY_EINVAL
+        assert f(r=0) == wx.WXPY_EINVAL
+        assert f(r=R + 4) == wx.WXPY_EINVAL
+        assert f(x=X + 4) == wx.WXPY_EINVAL
+        assert f(ws=0) == wx.WXPY_EINVAL
+        assert f(wsb=ws_need - 8) == wx.WXPY_EINVAL
+        assert f(ws=WS + 8) == wx.WXPY_EINVAL
+        assert f(w=X + 8) == wx.WXPY_EOVERLAP
+        assert f(r=W + 16) == wx.WXPY_EOVERLAP
+        assert f(ws=X + 64) == wx.WXPY_EOVERLAP
+    assert dot(z=0) == wx.WXPY_EINVAL
+    assert dot(w=Z + 8) == wx.WXPY_EOVERLAP
+    assert lib.wxpy_reduce_pipes(17) == wx.WXPY_EINVAL
+    assert lib.wxpy_reduce_pipes(-2) == wx.WXPY_EINVAL
+    assert lib.wxpy_reduce_pipes(-1) == 0

@@ -1,0 +1,169 @@
+"""GPU parity of the update fused with a reduction (wxpy_norm2, wxpy_dot)
+through the C ABI: w and the result bit for bit against the oracle of
+reduce_oracle.c (NaN by class) -- sizes around every tile boundary and
+several tiles per block, the 32-byte and element paths, exact aliasing,
+every product split, special values, the tree's worked examples, CUDA-graph
+replay, and the full n = 2^26 case compared in full."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import pins
+import paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import synth
+from gpu_util import Guarded
+
+pytestmark = pytest.mark.gpu
+
+T = 8192
+SIZES = (0, 1, 5, T - 1, T, T + 1, 3 * T + 77, 100003, 1_000_003)
+
+
+@pytest.fixture(autouse=True)
+def _pipes():
+    yield
+    wx.wxpy_reduce_pipes(-1)
+
+
+def same_scalar(got, want):
+    return (math.isnan(got) and math.isnan(want)) or pins.same_bits(got, want)
+
+
+def same_vec(got, want):
+    ok = (got.view(np.uint64) == want.view(np.uint64)) | (np.isnan(got) & np.isnan(want))
+    return bool(ok.all())
+
+
+def run(kind, alpha, xh, yh, zh, offs):
+    n = len(xh)
+    gx, gy, gw = Guarded(n, offs[0]).set(xh), Guarded(n, offs[1]).set(yh), Guarded(n, offs[2])
+    gz = Guarded(n, offs[3]).set(zh) if kind == "dot" else None
+    res = torch.full((1,), 12345.0, dtype=torch.float64, device="cuda")
+    if kind == "dot":
+        wx.wxpy_dot(alpha, gx.t, gy.t, gz.t, w=gw.t, result=res)
+    else:
+        wx.wxpy_norm2(alpha, gx.t, gy.t, w=gw.t, result=res)
+    torch.cuda.synchronize()
+    for g in (gx, gy, gw) + ((gz,) if gz else ()):
+        g.check()
+    return gw.t.cpu().numpy(), float(res.item())
+
+
+def want(kind, alpha, xh, yh, zh):
+    return oracle.wxpy_dot(alpha, xh, yh, zh) if kind == "dot" else oracle.wxpy_norm2(alpha, xh, yh)
+
+
+@pytest.mark.parametrize("kind", ["norm2", "dot"])
+@pytest.mark.parametrize("mul", [-1, 0, 5, 16])
+@pytest.mark.parametrize("offs", [(0, 0, 0, 0), (8, 8, 8, 8), (0, 16, 8, 24)])
+def test_parity(kind, mul, offs):
+    wx.wxpy_reduce_pipes(mul)
+    for n in SIZES:
+        alpha, xh, yh = synth.vectors(synth.BASE_SEED + 500 + n, n)
+        zh = synth.uniform_pm1(synth.BASE_SEED + 501 + n, synth.TAG_Y, n)
+        w_got, r_got = run(kind, alpha, xh, yh, zh, offs)
+        w_want, r_want = want(kind, alpha, xh, yh, zh)
+        assert same_vec(w_got, w_want), (kind, n, offs)
+        assert same_scalar(r_got, r_want), (kind, n, offs, r_got, r_want)
+
+
+@pytest.mark.parametrize("kind", ["norm2", "dot"])
+@pytest.mark.parametrize("mul", [0, 16])
+def test_special_and_wide_values(kind, mul):
+    wx.wxpy_reduce_pipes(mul)
+    sv = np.array(pins.special_values())
+    rng = np.random.default_rng(3)
+    for n in (len(sv) ** 2, 3 * T + 5):
+        x = np.resize(np.repeat(sv, len(sv)), n)
+        y = np.resize(np.tile(sv, len(sv)), n)
+        z = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-300, 300, n))
+        for alpha in (1.0, -0.75, 2.0 ** -600):
+            w_got, r_got = run(kind, alpha, x, y, z, (0, 0, 0, 0))
+            w_want, r_want = want(kind, alpha, x, y, z)
+            assert same_vec(w_got, w_want) and same_scalar(r_got, r_want), (kind, alpha, n)
+        # finite wide-exponent data: every branch of the integer product
+        x = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-500, 500, n))
+        y = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-500, 500, n))
+        w_got, r_got = run(kind, 1.5, x, y, z, (0, 0, 0, 0))
+        w_want, r_want = want(kind, 1.5, x, y, z)
+        assert same_vec(w_got, w_want) and same_scalar(r_got, r_want)
+
+
+def test_worked_examples_of_the_tree():
+    """The hand-derived cases of the oracle pins, on the GPU."""
+    b = 2.0 ** 53
+    for vals, pos, n, expect in (([b, -b, 1.0, 1.0], [0, 1, 4096, 4097], 4098, 1.0),
+                                 ([b, -b, 1.0, 1.0], [0, 1, T, T + 1], T + 2, 2.0),
+                                 ([b, 1.0, 1.0, -b], [0, T, 2 * T, 4 * T], 4 * T + 1, 2.0)):
+        x = np.zeros(n)
+        x[pos] = vals
+        _, r = run("dot", 1.0, x, np.zeros(n), np.ones(n), (0, 0, 0, 0))
+        assert r == expect
+    w = np.array([2.0 ** 27, 1, 0, 1, 0, 1, 0, 1])
+    _, r = run("norm2", 1.0, w, np.zeros(8), None, (0, 0, 0, 0))
+    assert r == 2.0 ** 54 + 4
+
+
+def test_aliasing():
+    n = 3 * T + 11
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + 77, n)
+    w_want, s_want = oracle.wxpy_norm2(alpha, xh, yh)
+    for target in ("x", "y"):
+        x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+        w = x if target == "x" else y
+        _, res = wx.wxpy_norm2(alpha, x, y, w=w)
+        torch.cuda.synchronize()
+        assert same_vec(w.cpu().numpy(), w_want) and same_scalar(res.item(), s_want)
+    # dot with z == w: z is read (the old w) before w is written
+    zh = synth.uniform_pm1(5, synth.TAG_Y, n)
+    x, y, z = (torch.from_numpy(a).cuda() for a in (xh, yh, zh))
+    _, d_want = oracle.wxpy_dot(alpha, xh, yh, zh)
+    _, res = wx.wxpy_dot(alpha, x, y, z, w=z)
+    torch.cuda.synchronize()
+    assert same_vec(z.cpu().numpy(), w_want) and same_scalar(res.item(), d_want)
+
+
+def test_graph_replay_and_determinism():
+    n = 5 * T + 3
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + 88, n)
+    x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+    w = torch.empty_like(x)
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = wx.reduce_workspace(n)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        wx.wxpy_norm2(alpha, x, y, w=w, result=res, workspace=ws, stream=s)  # warm-up outside capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        wx.wxpy_norm2(alpha, x, y, w=w, result=res, workspace=ws, stream=s)
+    _, want_s = oracle.wxpy_norm2(alpha, xh, yh)
+    for _ in range(3):
+        res.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert same_scalar(res.item(), want_s)
+
+
+def test_full_size():
+    """n = 2^26 on generator inputs: w and the result compared in full."""
+    n = 1 << 26
+    seed = synth.BASE_SEED + 90
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+    wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+    wx.wxpy_fill_uniform(z, seed + 1, synth.TAG_X)
+    xh, yh, zh = x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy()
+    for kind in ("norm2", "dot"):
+        if kind == "dot":
+            w, res = wx.wxpy_dot(-0.625, x, y, z)
+            w_want, r_want = oracle.wxpy_dot(-0.625, xh, yh, zh)
+        else:
+            w, res = wx.wxpy_norm2(-0.625, x, y)
+            w_want, r_want = oracle.wxpy_norm2(-0.625, xh, yh)
+        torch.cuda.synchronize()
+        assert same_vec(w.cpu().numpy(), w_want) and same_scalar(res.item(), r_want), kind
