@@ -167,3 +167,37 @@ def test_full_size():
             w_want, r_want = oracle.wxpy_norm2(-0.625, xh, yh)
         torch.cuda.synchronize()
         assert same_vec(w.cpu().numpy(), w_want) and same_scalar(res.item(), r_want), kind
+
+
+def test_concurrent_calls_on_separate_streams():
+    """Four fused reductions in flight at once on four streams, each with its
+    own workspace: every result is the oracle's."""
+    cases = []
+    for k in range(4):
+        n = (k + 1) * T * 3 + k
+        alpha, xh, yh = synth.vectors(synth.BASE_SEED + 900 + k, n)
+        zh = synth.uniform_pm1(synth.BASE_SEED + 910 + k, synth.TAG_Y, n)
+        x, y, z = (torch.from_numpy(a).cuda() for a in (xh, yh, zh))
+        cases.append((alpha, xh, yh, zh, x, y, z, torch.cuda.Stream(), wx.reduce_workspace(n)))
+    torch.cuda.synchronize()
+    outs = []
+    for k, (alpha, _, _, _, x, y, z, s, ws) in enumerate(cases):
+        with torch.cuda.stream(s):
+            if k % 2:
+                outs.append(wx.wxpy_dot(alpha, x, y, z, workspace=ws, stream=s))
+            else:
+                outs.append(wx.wxpy_norm2(alpha, x, y, workspace=ws, stream=s))
+    torch.cuda.synchronize()
+    for k, ((alpha, xh, yh, zh, *_), (w, res)) in enumerate(zip(cases, outs)):
+        w_want, r_want = (oracle.wxpy_dot(alpha, xh, yh, zh) if k % 2
+                          else oracle.wxpy_norm2(alpha, xh, yh))
+        assert same_vec(w.cpu().numpy(), w_want) and same_scalar(res.item(), r_want), k
+
+
+def test_small_workspace_is_refused():
+    n = 3 * T
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ws = torch.empty(wx.lib().wxpy_reduce_workspace_bytes(n) - 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy_norm2(1.0, x, x, workspace=ws)
+    assert e.value.status == wx.WXPY_EINVAL

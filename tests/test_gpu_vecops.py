@@ -264,3 +264,34 @@ def test_pipe_split_search_then_parity(tmp_path):
     finally:
         for c in range(wx.VEC_CLASSES):
             wx.wxpy_vecops_tuned_set(c, -1, -1)
+
+
+def test_stream_and_graph_capture():
+    """axpbypcz and maxpy on a non-default stream, captured in a CUDA graph and
+    replayed: each replay from restored inputs gives the oracle's bits."""
+    n = 3 * 1024 * 256 + 13  # several staged tiles per block
+    xh, yh, zh = (vals(950 + k, n, False) for k in range(3))
+    x, y, z = (torch.from_numpy(a).cuda() for a in (xh, yh, zh))
+    z0 = z.clone()
+    xs = [torch.from_numpy(vals(960 + j, n, False)).cuda() for j in range(3)]
+    al = [0.5, -1.25, 2.0]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        wx.wxpy_axpbypcz(0.75, -0.5, 1.5, x, y, z, stream=s)  # first call outside capture
+        wx.wxpy_maxpy(al, xs, y, stream=s)
+    s.synchronize()
+    y.copy_(torch.from_numpy(yh))
+    z.copy_(z0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        wx.wxpy_axpbypcz(0.75, -0.5, 1.5, x, y, z, stream=s)
+        wx.wxpy_maxpy(al, xs, y, stream=s)
+    z_want = oracle.axpbypcz(0.75, -0.5, 1.5, xh, yh, zh)
+    y_want = oracle.maxpy(al, [t.cpu().numpy() for t in xs], yh)
+    for _ in range(2):
+        y.copy_(torch.from_numpy(yh))
+        z.copy_(z0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert same(z, z_want) and same(y, y_want)
+    wx.wxpy_vecops_status()
