@@ -791,6 +791,7 @@ def measure_cpu_family():
 
 
 SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)
+SERVE_BACKFILL_US = 5000
 
 
 def measure_served(seconds):
@@ -801,15 +802,21 @@ def measure_served(seconds):
     from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL
     from paper_1309_1894_gb300 import synth
     out = {"budget_gib": 16, "n_range": [1 << 8, 1 << 24], "seconds_per_rate": seconds,
-           "rates": list(SERVE_RATES), "batched": [], "serial": []}
-    for name, mode in (("batched", SERVE_BATCHED), ("serial", SERVE_SERIAL)):
+           "rates": list(SERVE_RATES), "backfill_aging_us": SERVE_BACKFILL_US,
+           "batched": [], "batched_backfill": [], "serial": []}
+    for name, mode, admission in (("batched", SERVE_BATCHED, 0),
+                                  ("batched_backfill", SERVE_BATCHED, SERVE_BACKFILL_US),
+                                  ("serial", SERVE_SERIAL, 0)):
         with Server(budget_bytes=16 << 30, max_slots=4096, n_streams=2, max_batch=1024,
-                    max_queue=65536, mode=mode) as sv:
+                    max_queue=65536, mode=mode, admission_us=admission) as sv:
             for i, rate in enumerate(SERVE_RATES):
                 r = sv.loadgen(rate=rate, duration_s=seconds, n_min=1 << 8, n_max=1 << 24,
                                seed=synth.BASE_SEED + 100 + i, drain_timeout_s=120.0,
                                check_drain=False)
+                st = sv.stats()
                 out[name].append({
+                    "head_wait_frag_s": st["head_wait_frag_s"],
+                    "head_wait_full_s": st["head_wait_full_s"], "backfilled": st["backfilled"],
                     "rate": rate, "offered": r["offered"], "completed": r["completed"],
                     "rejected": r["rejected"], "failed": r["failed"],
                     "p50_ms": r["p50_s"] * 1e3, "p99_ms": r["p99_s"] * 1e3,
@@ -877,8 +884,9 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="profiling mode: force this variant id instead of the tuned one")
     ap.add_argument("--vecop", default="",
-                    help="profiling mode: only run this sibling kernel (axpbypcz, maxpy4, "
-                         "maxpy8, pointwise_mult, norm2, dot) on n = SINGLE, --reps times")
+                    help="profiling mode: only run this kernel (axpbypcz, maxpy4, maxpy8, "
+                         "pointwise_mult, norm2, dot; serve: one 64-request server batch with "
+                         "n up to SINGLE) on n = SINGLE, --reps times")
     ap.add_argument("--pipes", default="-1,-1",
                     help="profiling mode: add offload and product sixteenths for --vecop")
     args = ap.parse_args()
@@ -927,12 +935,27 @@ def run_vecop(args):
     from paper_1309_1894_gb300 import synth
     n = args.single
     nvec = {"axpbypcz": 3, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3, "norm2": 3,
-            "dot": 4}[args.vecop]
+            "dot": 4, "serve": 1}[args.vecop]
     v = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(nvec)]
     for k, t in enumerate(v):
         wx.wxpy_fill_uniform(t, synth.BASE_SEED + k, synth.TAG_X)
     add, mul = (int(t) for t in args.pipes.split(","))
     wx.wxpy_vecops_pipes(add, mul)
+    if args.vecop == "serve":
+        # one batch through the server: 64 requests, n log-uniform in [2^8, n]
+        from paper_1309_1894_gb300.server import Server
+        del v
+        lens = synth.log_uniform_lengths(synth.BASE_SEED + 7, 64, 1 << 8, n)
+        with Server(budget_bytes=max(1 << 30, 24 * int(sum(lens)) + (64 << 20)), max_slots=64,
+                    n_streams=1, max_batch=64) as sv:
+            for _ in range(args.reps):
+                tickets = [sv.submit(int(m), 0.75, synth.BASE_SEED + k) for k, m in enumerate(lens)]
+                for t in tickets:
+                    sv.wait(t)
+                    sv.release(t)
+        print(json.dumps({"vecop": "serve", "n_max": n, "requests": 64, "reps": args.reps}),
+              flush=True)
+        return 0
     if args.vecop in ("norm2", "dot"):
         ws = wx.reduce_workspace(n)
         res = torch.empty(1, dtype=torch.float64, device="cuda")

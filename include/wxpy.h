@@ -544,10 +544,17 @@ typedef struct wxpy_server_config {
                              different streams overlap on the device */
     int32_t max_batch;    /* requests coalesced into one batched launch */
     int32_t max_queue;    /* queued requests beyond which submit refuses (EBUSY) */
-    int32_t mode;         /* WXPY_SERVE_BATCHED: fill + one segmented launch per
-                             batch; WXPY_SERVE_SERIAL: per-request launches, the
-                             baseline */
-    int32_t reserved;
+    int32_t mode;         /* WXPY_SERVE_BATCHED: one segmented launch per batch
+                             that generates the inputs and computes w;
+                             WXPY_SERVE_SERIAL: per-request launches (fill x,
+                             fill y, wxpy()), the baseline */
+    int32_t admission;    /* 0: strict arrival order -- a request that does not
+                             fit the arena waits, and nothing passes it;
+                             > 0: backfill -- while the queue's head does not
+                             fit, later requests (up to 64 places back) that fit
+                             are admitted, for at most `admission`
+                             microseconds of the head's wait; after that nothing
+                             passes it until it is admitted */
 } wxpy_server_config;
 
 typedef struct wxpy_server wxpy_server; /* opaque */
@@ -560,6 +567,11 @@ typedef struct wxpy_server_stats {
     double mean_batch;   /* requests per batch */
     double window_s;     /* time since the statistics were last reset */
     double p50_s, p99_s, mean_s, max_s; /* submit -> completion, completed requests */
+    double head_wait_frag_s;  /* time the queue's head waited although the arena
+                                 had enough free bytes in total (fragmentation) */
+    double head_wait_full_s;  /* time it waited because the arena was too full */
+    int64_t backfilled;       /* requests admitted ahead of a waiting head */
+    int64_t reserved;
 } wxpy_server_stats;
 
 /* Allocates the arena (cudaMalloc of budget_bytes), per-stream staging, and

@@ -26,16 +26,21 @@ __host__ __device__ __forceinline__ uint64_t stream_key_of(uint64_t seed, uint32
 // (a conversion, a multiply and an add per value would use it three times).
 // More generally, for a range of width 2^(s+1) centred on zero, the value
 // lo + width*u = m * 2^(s-53); `uniform_sym(key, i, s)` assembles that.
+// Every path stays an integer bit pattern until one opaque move into a double
+// register at the end.  Seen through, the sign bit OR-ed into the assembled
+// pattern was compiled as an FP64 negation (measured: one DADD per value).
 __device__ __forceinline__ double uniform_sym(uint64_t key, int64_t i, int s) {
     const uint64_t b = mix64(key + (uint64_t)(i + 1) * kGolden);
     const int64_t m = (int64_t)((b >> 11) << 1) - ((int64_t)1 << 53);  // [-2^53, 2^53), even
-    if (m == 0) return 0.0;
     const uint64_t sign = m < 0 ? (1ull << 63) : 0ull;
-    const uint64_t a = (uint64_t)(m < 0 ? -m : m);  // [2, 2^53]
-    const int p = 63 - __clzll((long long)a);      // a = 1.f * 2^p, p in [1, 53]
+    const uint64_t a = (uint64_t)(m < 0 ? -m : m);  // 0 or [2, 2^53]
+    const int p = 63 - __clzll((long long)(a | 1));  // a = 1.f * 2^p, p in [1, 53] (a > 0)
     const uint64_t frac = (p <= 52 ? (a << (52 - p)) : (a >> (p - 52))) & ((1ull << 52) - 1);
     const uint64_t expo = (uint64_t)(p - 53 + s + 1023);
-    return __longlong_as_double((long long)(sign | (expo << 52) | frac));
+    const uint64_t bits = m == 0 ? 0ull : (sign | (expo << 52) | frac);
+    double v;
+    asm("mov.b64 %0, %1;" : "=d"(v) : "l"(bits));
+    return v;
 }
 
 __device__ __forceinline__ double uniform_pm1(uint64_t key, int64_t i) {

@@ -3,12 +3,16 @@
 // Clients submit requests (n, alpha, seed).  A scheduler thread
 //   1. admits queued requests in arrival order while the device-memory budget
 //      (one arena, first fit, 256-byte blocks holding x, y, w) and the slot
-//      limit allow -- a request waits, it is never reordered past;
+//      limit allow.  Strict order (admission = 0): a request that does not
+//      fit waits, and nothing passes it.  Backfill (admission = A > 0 us):
+//      while the head does not fit, later requests that do are admitted ahead
+//      of it, for at most A us of the head's wait -- then the head holds the
+//      line until memory frees, so it cannot starve;
 //   2. coalesces every admitted, not yet launched request (up to max_batch)
-//      into one batch and launches it on the next free stream: a segmented
-//      fill of the inputs from the request seeds, then the segmented WXPY
-//      kernel over the same tile list -- two launches per batch, whatever the
-//      number of requests in it;
+//      into one batch and launches it on the next free stream: one segmented
+//      kernel that generates each request's inputs from its seed and computes
+//      its w in the same pass -- one launch per batch, whatever the number of
+//      requests in it;
 //   3. polls the batches' completion events, stamps each request's completion
 //      time, and frees the buffers of requests marked auto-release.
 // Requests that arrive while batches run on other streams are admitted and
@@ -35,9 +39,9 @@
 #include <unordered_map>
 #include <vector>
 
+#include "fp64_mul.cuh"
 #include "gen.cuh"
 #include "internal.h"
-#include "seg_tile.cuh"
 
 namespace wx {
 namespace {
@@ -146,11 +150,44 @@ __device__ __forceinline__ int64_t find_request(const ServePlan *plan, int64_t c
     return lo;
 }
 
-// Generates x and y of every request of a batch, tile by tile.
-__global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
-                                                         const uint64_t *seeds,
-                                                         const ServePlan *plan, int64_t count,
-                                                         int64_t ntiles) {
+// One pass per batch: for every element of every request, generate x and y
+// from the request's seed, compute w = RN(RN(alpha*x) + y), and store all
+// three (the request's result is x, y and w).  A warp takes a tile; a lane
+// takes four consecutive elements and writes them as 32-byte vectors (tiles
+// start at multiples of their length, a multiple of 4, in 256-byte-aligned
+// buffers), the ragged end of a tile element by element.  Generating in
+// registers saves writing x and y and reading them back (40 bytes per
+// element in two passes become 24 in one).  PM: the products alpha*x run in
+// the integer pipelines at no (0), odd (1) or every (2) position of a vector,
+// fixed at compile time; the sums stay in FP64.
+__device__ __forceinline__ uint64_t bits_of_d(double v) { return (uint64_t)__double_as_longlong(v); }
+
+template <int PM>
+__device__ __forceinline__ double serve_elem(double alpha, const MulCoef &ca, double x, double y,
+                                             int q) {
+    double p;
+    if (PM == 2 || (PM == 1 && (q & 1))) {
+        bool slow = false;
+        uint64_t pb = mul_rn_core(ca, bits_of_d(x), slow);
+        if (slow) pb = mul_rn_hw_bits(bits_of_d(alpha), bits_of_d(x));
+        p = __longlong_as_double((long long)pb);
+    } else {
+        p = __dmul_rn(alpha, x);
+    }
+    return __dadd_rn(p, y);
+}
+
+__device__ __forceinline__ void st4_cs(double *p, double a, double b, double c, double d) {
+    asm volatile("st.global.cs.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a), "d"(b), "d"(c),
+                 "d"(d)
+                 : "memory");
+}
+
+template <int PM>
+__global__ void __launch_bounds__(256) serve_fused_kernel(const wxpy_desc *table,
+                                                          const uint64_t *seeds,
+                                                          const ServePlan *plan, int64_t count,
+                                                          int64_t ntiles) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -162,33 +199,36 @@ __global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
         const int64_t begin = (t - sp.first_tile) * sp.tile_len;
         const int64_t end = min(d.n, begin + sp.tile_len);
         const uint64_t kx = stream_key_of(seeds[s], 1), ky = stream_key_of(seeds[s], 2);
-        double *x = const_cast<double *>(d.x), *y = const_cast<double *>(d.y);
-        for (int64_t i = begin + lane; i < end; i += 32) {
-            x[i] = uniform_pm1(kx, i);
-            y[i] = uniform_pm1(ky, i);
+        const MulCoef ca = mul_coef_of(bits_of_d(d.alpha));
+        double *x = const_cast<double *>(d.x), *y = const_cast<double *>(d.y), *w = d.w;
+        const int64_t nvec = (end - begin) >> 2;
+        for (int64_t c = lane; c < nvec; c += 32) {
+            const int64_t i0 = begin + 4 * c;
+            double xv[4], yv[4], wv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xv[q] = uniform_pm1(kx, i0 + q);
+                yv[q] = uniform_pm1(ky, i0 + q);
+                wv[q] = serve_elem<PM>(d.alpha, ca, xv[q], yv[q], q);
+            }
+            st4_cs(x + i0, xv[0], xv[1], xv[2], xv[3]);
+            st4_cs(y + i0, yv[0], yv[1], yv[2], yv[3]);
+            st4_cs(w + i0, wv[0], wv[1], wv[2], wv[3]);
+        }
+        for (int64_t i = begin + 4 * nvec + lane; i < end; i += 32) {
+            const double xi = uniform_pm1(kx, i), yi = uniform_pm1(ky, i);
+            x[i] = xi;
+            y[i] = yi;
+            w[i] = serve_elem<0>(d.alpha, ca, xi, yi, 0);
         }
     }
 }
 
-// w = RN(RN(alpha*x) + y) for every request of a batch, tile by tile.
-template <int EMU>
-__global__ void __launch_bounds__(256, 2) serve_wxpy_kernel(const wxpy_desc *table,
-                                                            const ServePlan *plan, int64_t count,
-                                                            int64_t ntiles) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int64_t s = 0;
-    for (int64_t t = warp; t < ntiles; t += nwarps) {
-        s = find_request(plan, count, t, s);
-        const wxpy_desc d = table[s];
-        const ServePlan sp = plan[s];
-        const int64_t begin = (t - sp.first_tile) * sp.tile_len;
-        const int64_t len = min(sp.tile_len, d.n - begin);
-        if (len > 0)
-            tile_wxpy<EMU>(d.x + begin, d.y + begin, d.w + begin, d.alpha, len, lane, 1 << sp.ulog);
-    }
-}
+// Saturated Poisson load on GB300 (n log-uniform in [2^8, 2^24]): 2.09e11
+// elements/s with every product in FP64, 1.82e11 with half, 1.59e11 with all
+// in the integer pipelines -- the generator keeps the ALU pipe busy and
+// leaves FP64 free.
+constexpr int kServePM = 0;
 
 }  // namespace
 }  // namespace wx
@@ -218,7 +258,13 @@ struct wxpy_server {
     int64_t submitted = 0, rejected = 0, completed = 0, failed = 0, max_queue = 0;
     int64_t batches = 0, launches = 0, elements_done = 0, requests_launched = 0;
     int64_t max_inflight = 0;  // most batches on the device at once
+    int64_t backfilled = 0;
+    double head_wait_frag = 0, head_wait_full = 0;  // seconds
     std::vector<double> latencies;
+
+    // the queue head's wait: since when, and the last time it was accounted
+    uint64_t waiting_head = 0;
+    Clock::time_point head_since, head_accounted;
 
     std::thread sched;
     std::atomic<bool> stop{false};
@@ -321,21 +367,14 @@ cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> 
                             s.stream);
     if (e != cudaSuccess) return e;
     const int64_t wpb = 256 / 32;
-    const unsigned fill_grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)8 * sv->sm_count, (ntiles + wpb - 1) / wpb));
     const unsigned grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)shape.blocks_per_sm * sv->sm_count, (ntiles + wpb - 1) / wpb));
+        1, std::min<int64_t>((int64_t)8 * sv->sm_count, (ntiles + wpb - 1) / wpb));
     e = injected_launch_error();
     if (e != cudaSuccess) return e;
-    serve_fill_kernel<<<fill_grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
-                                                       ntiles);
+    serve_fused_kernel<kServePM><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
+                                                             ntiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (shape.offload)
-        serve_wxpy_kernel<1><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
-    else
-        serve_wxpy_kernel<0><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_plan, count, ntiles);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    sv->launches += 2;
+    sv->launches += 1;
     return cudaEventRecord(s.done, s.stream);
 }
 
@@ -354,24 +393,61 @@ void scheduler(wxpy_server *sv) {
             retire_slot(sv, s, now, q == cudaSuccess ? 0 : (int)q);
             progress = true;
         }
-        // 2. admission, in arrival order
+        // 2. admission, in arrival order (with backfill ahead of a blocked head)
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            while (!sv->queue.empty() && sv->resident < sv->cfg.max_slots) {
-                Request &r = sv->reqs[sv->queue.front()];
+            auto admit = [&](uint64_t ticket, int64_t off) {
+                Request &r = sv->reqs[ticket];
                 const int64_t vb = round_up(r.n * 8, kBlock);
-                const int64_t off = sv->arena.alloc(3 * vb);
-                if (off < 0) break;  // wait for memory; no reordering
                 r.off = off;
                 r.bytes = 3 * vb;
                 r.x = (double *)(sv->arena_base + off);
                 r.y = (double *)(sv->arena_base + off + vb);
                 r.w = (double *)(sv->arena_base + off + 2 * vb);
                 r.state = kAdmitted;
-                sv->admitted.push_back(sv->queue.front());
-                sv->queue.pop_front();
+                sv->admitted.push_back(ticket);
                 ++sv->resident;
                 progress = true;
+            };
+            while (!sv->queue.empty() && sv->resident < sv->cfg.max_slots) {
+                const uint64_t head = sv->queue.front();
+                const int64_t need = 3 * round_up(sv->reqs[head].n * 8, kBlock);
+                const int64_t off = sv->arena.alloc(need);
+                const Clock::time_point now = Clock::now();
+                if (off >= 0) {
+                    // (its wait is accounted up to the previous scheduler pass)
+                    if (sv->waiting_head == head) sv->waiting_head = 0;
+                    sv->queue.pop_front();
+                    admit(head, off);
+                    continue;
+                }
+                // the head waits: account the time since the last check by cause
+                if (sv->waiting_head != head) {
+                    sv->waiting_head = head;
+                    sv->head_since = sv->head_accounted = now;
+                } else {
+                    const double dt = seconds(now - sv->head_accounted);
+                    if (sv->arena.size() - sv->arena.used() >= need) sv->head_wait_frag += dt;
+                    else sv->head_wait_full += dt;
+                    sv->head_accounted = now;
+                }
+                const int32_t aging = sv->cfg.admission;
+                if (aging > 0 && seconds(now - sv->head_since) * 1e6 < (double)aging) {
+                    // backfill: later requests that fit, up to 64 places back
+                    for (size_t k = 1; k < sv->queue.size() && k <= 64 &&
+                                       sv->resident < sv->cfg.max_slots;) {
+                        const uint64_t t = sv->queue[k];
+                        const int64_t off2 = sv->arena.alloc(3 * round_up(sv->reqs[t].n * 8, kBlock));
+                        if (off2 < 0) {
+                            ++k;
+                            continue;
+                        }
+                        sv->queue.erase(sv->queue.begin() + (std::ptrdiff_t)k);
+                        admit(t, off2);
+                        ++sv->backfilled;
+                    }
+                }
+                break;
             }
         }
         // 3. launch the admitted requests on a free stream
@@ -489,7 +565,7 @@ int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out) {
     *out = nullptr;
     if (cfg->budget_bytes < 3 * kBlock || cfg->max_slots < 1 || cfg->n_streams < 1 ||
         cfg->n_streams > 16 || cfg->max_batch < 1 || cfg->max_queue < 1 ||
-        (cfg->mode != WXPY_SERVE_BATCHED && cfg->mode != WXPY_SERVE_SERIAL))
+        (cfg->mode != WXPY_SERVE_BATCHED && cfg->mode != WXPY_SERVE_SERIAL) || cfg->admission < 0)
         return fail(WXPY_EINVAL, "bad server configuration");
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);
@@ -618,7 +694,13 @@ int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
     }
     out->mean_s = sv->latencies.empty() ? 0.0 : sum / (double)sv->latencies.size();
     out->max_s = mx;
+    out->head_wait_frag_s = sv->head_wait_frag;
+    out->head_wait_full_s = sv->head_wait_full;
+    out->backfilled = sv->backfilled;
+    out->reserved = 0;
     if (reset) {
+        sv->head_wait_frag = sv->head_wait_full = 0;
+        sv->backfilled = 0;
         sv->submitted = sv->rejected = sv->completed = sv->failed = 0;
         sv->batches = sv->launches = sv->elements_done = sv->requests_launched = 0;
         sv->max_inflight = 0;

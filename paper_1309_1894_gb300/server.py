@@ -17,7 +17,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("admission", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -25,7 +25,8 @@ class ServerStats(ctypes.Structure):
         "submitted", "rejected", "completed", "failed", "queued_now", "resident_now",
         "max_queue", "batches", "launches", "elements_done", "arena_used", "max_inflight")] + \
         [(f, ctypes.c_double) for f in ("mean_batch", "window_s", "p50_s", "p99_s", "mean_s",
-                                        "max_s")]
+                                        "max_s", "head_wait_frag_s", "head_wait_full_s")] + \
+        [("backfilled", ctypes.c_int64), ("reserved", ctypes.c_int64)]
 
 
 class LoadgenConfig(ctypes.Structure):
@@ -51,8 +52,11 @@ class Server:
     """A running wxpy server (wxpy_server_create ... wxpy_server_destroy)."""
 
     def __init__(self, budget_bytes: int = 16 << 30, max_slots: int = 4096, n_streams: int = 2,
-                 max_batch: int = 1024, max_queue: int = 65536, mode: int = SERVE_BATCHED):
-        cfg = ServerConfig(budget_bytes, max_slots, n_streams, max_batch, max_queue, mode, 0)
+                 max_batch: int = 1024, max_queue: int = 65536, mode: int = SERVE_BATCHED,
+                 admission_us: int = 0):
+        """admission_us: 0 strict arrival order; > 0 backfill with that aging bound (us)."""
+        cfg = ServerConfig(budget_bytes, max_slots, n_streams, max_batch, max_queue, mode,
+                           admission_us)
         h = _P()
         check(lib().wxpy_server_create(ctypes.byref(cfg), ctypes.byref(h)), "wxpy_server_create")
         self.handle = h.value
