@@ -92,6 +92,14 @@ int wxpy_cpu_tune_get(int bucket, int *variant_id);
 int wxpy_cpu_tune_set(int bucket, int variant_id);
 int wxpy_cpu_tune_clear(void);
 
+/* The table as JSON ("wxpy-cpu-tune-1"), keyed by the machine it was tuned on
+ * (architecture, online CPU count, the target flavour's flags): the search's
+ * result persisted for later processes.  load applies nothing unless every
+ * entry is valid; with check_machine it refuses a file from another machine.
+ * Errors: WXPY_EINVAL (unwritable, malformed, other machine), WXPY_ENOTFOUND. */
+int wxpy_cpu_tune_cache_save(const char *path);
+int wxpy_cpu_tune_cache_load(const char *path, int check_machine);
+
 /* Text of the last error on this thread. */
 const char *wxpy_cpu_last_error(void);
 

@@ -254,6 +254,109 @@ int wxpy_cpu_tune_clear(void) {
     return WXPY_OK;
 }
 
+/* ---- the tuning table on disk ------------------------------------------------ */
+
+/* The machine a table is valid for: architecture, online CPU count, and the
+ * flags of the target flavour (variant ids index the flavour list). */
+static void machine_key(char *buf, size_t len) {
+    const char *arch =
+#if defined(__aarch64__)
+        "aarch64";
+#elif defined(__x86_64__)
+        "x86_64";
+#else
+        "other";
+#endif
+    snprintf(buf, len, "%s|cpus%d|%s", arch, g_thr_opts[thread_options() - 1], kFlavourFlags[2]);
+}
+
+int wxpy_cpu_tune_cache_save(const char *path) {
+    if (!path) return fail(WXPY_EINVAL, "null path");
+    char key[256], tmp[4096];
+    machine_key(key, sizeof key);
+    snprintf(tmp, sizeof tmp, "%s.tmp", path);
+    FILE *f = fopen(tmp, "wb");
+    if (!f) return fail(WXPY_EINVAL, "cannot write %s", tmp);
+    int ok = fprintf(f, "{\n  \"format\": \"wxpy-cpu-tune-1\",\n  \"machine\": \"%s\",\n"
+                        "  \"entries\": [", key) > 0;
+    int first = 1;
+    for (int b = 0; b < 64 && ok; ++b) {
+        const int id = atomic_load(&g_tuned[b]);
+        if (id < 0) continue;
+        wxpy_cpu_variant_info v;
+        if (wxpy_cpu_variant_describe(id, &v) != WXPY_OK) continue;
+        ok = fprintf(f, "%s\n    {\"bucket\": %d, \"variant\": %d, \"flavour\": %d, "
+                        "\"kernel\": %d, \"threads\": %d}",
+                     first ? "" : ",", b, id, v.flavour, v.kernel, v.threads) > 0;
+        first = 0;
+    }
+    ok = ok && fprintf(f, "\n  ]\n}\n") > 0;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp, path) != 0) return fail(WXPY_EINVAL, "cannot write %s", path);
+    return WXPY_OK;
+}
+
+/* Value of integer field `name` inside [from, to) of s; 0 when absent. */
+static int find_int_field(const char *from, const char *to, const char *name, long *out) {
+    char pat[64];
+    snprintf(pat, sizeof pat, "\"%s\"", name);
+    const char *p = strstr(from, pat);
+    if (!p || p >= to) return 0;
+    p = strchr(p + strlen(pat), ':');
+    if (!p || p >= to) return 0;
+    char *end = NULL;
+    errno = 0;
+    const long v = strtol(p + 1, &end, 10);
+    if (errno || end == p + 1 || end > to) return 0;
+    *out = v;
+    return 1;
+}
+
+int wxpy_cpu_tune_cache_load(const char *path, int check_machine) {
+    if (!path) return fail(WXPY_EINVAL, "null path");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(WXPY_ENOTFOUND, "cannot open %s", path);
+    char *s = malloc(1 << 20);
+    if (!s) {
+        fclose(f);
+        return fail(WXPY_ENOMEM, "cache buffer");
+    }
+    const size_t len = fread(s, 1, (1 << 20) - 1, f);
+    fclose(f);
+    s[len] = 0;
+    int st = WXPY_OK;
+    if (!strstr(s, "\"format\": \"wxpy-cpu-tune-1\"")) st = fail(WXPY_EINVAL, "%s: not a cpu tune cache", path);
+    if (st == WXPY_OK && check_machine) {
+        char key[256], pat[300];
+        machine_key(key, sizeof key);
+        snprintf(pat, sizeof pat, "\"machine\": \"%s\"", key);
+        if (!strstr(s, pat)) st = fail(WXPY_EINVAL, "%s was tuned on another machine", path);
+    }
+    /* parse every entry first; apply only if all are valid */
+    int ids[64];
+    for (int b = 0; b < 64; ++b) ids[b] = -2;
+    const char *p = st == WXPY_OK ? strstr(s, "\"entries\"") : NULL;
+    if (st == WXPY_OK && !p) st = fail(WXPY_EINVAL, "%s: no entries", path);
+    const char *end = p ? strchr(p, ']') : NULL;
+    if (st == WXPY_OK && !end) st = fail(WXPY_EINVAL, "%s: unterminated entries", path);
+    while (st == WXPY_OK && (p = strchr(p + 1, '{')) != NULL && p < end) {
+        const char *q = strchr(p, '}');
+        long b = -1, id = -1;
+        if (!q || q > end || !find_int_field(p, q, "bucket", &b) ||
+            !find_int_field(p, q, "variant", &id) || b < 0 || b >= 64 || id < 0 ||
+            id >= wxpy_cpu_variant_count())
+            st = fail(WXPY_EINVAL, "%s: malformed entry", path);
+        else
+            ids[b] = (int)id;
+        p = q;
+    }
+    free(s);
+    if (st != WXPY_OK) return st;
+    for (int b = 0; b < 64; ++b)
+        if (ids[b] >= 0) atomic_store(&g_tuned[b], ids[b]);
+    return WXPY_OK;
+}
+
 /* ---- the search ------------------------------------------------------------ */
 
 static double now_us(void) {

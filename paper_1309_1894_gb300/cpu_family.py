@@ -62,6 +62,8 @@ SIGNATURES = {
     "wxpy_cpu_tune_set": (_INT, [_INT, _INT]),
     "wxpy_cpu_tune_clear": (_INT, []),
     "wxpy_cpu_last_error": (ctypes.c_char_p, []),
+    "wxpy_cpu_tune_cache_save": (_INT, [ctypes.c_char_p]),
+    "wxpy_cpu_tune_cache_load": (_INT, [ctypes.c_char_p, _INT]),
 }
 
 
@@ -152,3 +154,11 @@ def tune_set(bucket: int, variant: int) -> None:
 
 def tune_clear() -> None:
     _check(lib().wxpy_cpu_tune_clear(), "tune_clear")
+
+
+def tune_cache_save(path: str) -> None:
+    _check(lib().wxpy_cpu_tune_cache_save(path.encode()), "tune_cache_save")
+
+
+def tune_cache_load(path: str, check_machine: bool = True) -> None:
+    _check(lib().wxpy_cpu_tune_cache_load(path.encode(), int(check_machine)), "tune_cache_load")

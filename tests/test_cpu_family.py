@@ -159,3 +159,39 @@ def test_search_then_lookup():
         cf.tune_set(64, 0)
     with pytest.raises(WxpyError):
         cf.tune_set(3, cf.variant_count())
+
+
+def test_tune_cache_round_trip_and_refusals(tmp_path):
+    import json
+    cf.tune_clear()
+    cf.tune_set(12, 5)
+    cf.tune_set(20, cf.variant_count() - 1)
+    path = str(tmp_path / "cpu.json")
+    cf.tune_cache_save(path)
+    doc = json.load(open(path))
+    assert doc["format"] == "wxpy-cpu-tune-1" and len(doc["entries"]) == 2
+    cf.tune_clear()
+    cf.tune_cache_load(path)
+    assert cf.tune_get(12) == 5 and cf.tune_get(20) == cf.variant_count() - 1
+    # another machine's file is refused unless the check is off
+    doc["machine"] = "elsewhere"
+    other = tmp_path / "other.json"
+    other.write_text(json.dumps(doc))
+    cf.tune_clear()
+    with pytest.raises(WxpyError) as e:
+        cf.tune_cache_load(str(other))
+    assert e.value.status == 1 and cf.tune_get(12) == -1
+    cf.tune_cache_load(str(other), check_machine=False)
+    assert cf.tune_get(12) == 5
+    # a malformed entry stores nothing
+    doc["entries"].append({"bucket": 70, "variant": 1})
+    bad = tmp_path / "bad.json"
+    bad.write_text(json.dumps(doc))
+    cf.tune_clear()
+    with pytest.raises(WxpyError):
+        cf.tune_cache_load(str(bad), check_machine=False)
+    assert cf.tune_get(12) == -1
+    with pytest.raises(WxpyError) as e:
+        cf.tune_cache_load(str(tmp_path / "missing.json"))
+    assert e.value.status == 7
+    cf.tune_clear()
