@@ -24,7 +24,6 @@ timing is the max over ranks and ``value`` the sum of all ranks' bytes.
 from __future__ import annotations
 
 import argparse
-import ctypes
 import hashlib
 import json
 import os

@@ -71,7 +71,7 @@ const DeviceProps *current_device(int *status) {
         p.cc_minor = prop.minor;
         p.l2_bytes = prop.l2CacheSize;
         p.global_bytes = (int64_t)prop.totalGlobalMem;
-        std::snprintf(p.name, sizeof p.name, "%s", prop.name);
+        std::snprintf(p.name, sizeof p.name, "%.127s", prop.name);  // the field holds 127 chars
     });
     if (g_dev_err[dev] != cudaSuccess) {
         *status = fail_cuda(g_dev_err[dev], "cudaGetDeviceProperties");

@@ -1,5 +1,4 @@
 """Helpers to read the C ABI declared under include/ (used by the ABI tests)."""
-import glob
 import os
 import re
 

@@ -1,6 +1,5 @@
 """Host-side logic of the batched launch (no GPU): descriptor validation runs
 before any CUDA call, and the batch shape table."""
-import numpy as np
 import pytest
 
 import paper_1309_1894_gb300 as wx

@@ -7,7 +7,6 @@ ranks) and of the work (sum over ranks).  Those run here as two gloo ranks.
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

@@ -3,7 +3,6 @@
 The search must reject no variant (every family member reproduces the
 reference results bit for bit), store its winner in the cell of the call's
 size bucket and class, and the tuned path must still match the oracle."""
-import numpy as np
 import pytest
 import torch
 

@@ -10,7 +10,7 @@ import torch
 import oracle
 import paper_1309_1894_gb300 as wx
 from paper_1309_1894_gb300 import synth
-from gpu_util import Guarded, bits_equal
+from gpu_util import Guarded
 from test_vecops_oracle import wide
 
 pytestmark = pytest.mark.gpu

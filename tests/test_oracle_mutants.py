@@ -5,7 +5,6 @@ mistakes a reader would look for when checking the oracle against the paper's
 definition -- compiled on the CPU into a temporary library.  The pins of
 ``tests/pins.py`` must reject every one of them, and accept the real oracle.
 """
-import os
 
 import pytest
 

@@ -7,7 +7,6 @@ point wxpy_batch() -- the tolerance of every parity test here is 0 ULP -- on
 two calls in a row with different tables, since both calls share one fixed
 scratch array inside the library.  This file is collected last on purpose.
 """
-import numpy as np
 import pytest
 import torch
 
