@@ -375,6 +375,8 @@ int wxpy_batch_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *s
 int wxpy_batch_graph_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table,
                             void *stream);
 
+/* The plan's shape (segments, elements, tiles, grid; see wxpy_batch_info),
+ * read from the host copy; touches no device.  WXPY_EINVAL for null. */
 int wxpy_batch_plan_info(const wxpy_batch_plan *plan, wxpy_batch_info *out);
 
 /* Reads (synchronously) the plan's status word: bit 0 set if a launch skipped

@@ -64,6 +64,9 @@ int wxpy_cpu(int64_t n, double alpha, const double *x, const double *y, double *
 int wxpy_cpu_run_variant(int id, int64_t n, double alpha, const double *x, const double *y,
                          double *w);
 
+/* Number of variants (3 flavours x 13 kernels x the thread counts of this
+ * machine), and the fields of variant `id` (WXPY_EINVAL out of range).  The
+ * `flags` string is static. */
 int wxpy_cpu_variant_count(void);
 int wxpy_cpu_variant_describe(int id, wxpy_cpu_variant_info *out);
 /* The paper's baseline (flavour 1, plain loop, one thread) and the reference
