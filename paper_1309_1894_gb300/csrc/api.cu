@@ -2,6 +2,8 @@
 // classification, the variant space, lookup, launch and the stream split.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -10,6 +12,7 @@
 #include <unordered_map>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace wx {
 
@@ -47,6 +50,14 @@ std::once_flag g_dev_once[kMaxDevices];
 DeviceProps g_dev[kMaxDevices];
 cudaError_t g_dev_err[kMaxDevices];
 }  // namespace
+
+bool trace_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("WXPY_NVTX");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
 
 const DeviceProps *current_device(int *status) {
     int dev = 0;

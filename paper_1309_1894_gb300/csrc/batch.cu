@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 #include "seg_tile.cuh"
 
 namespace wx {
@@ -263,6 +264,7 @@ int wxpy_batch_plan_create(const wxpy_desc *host_table, int64_t count, wxpy_batc
 }
 
 int wxpy_batch_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *stream) {
+    TraceRange trace("wxpy_batch_launch");
     if (!plan) return fail(WXPY_EINVAL, "null plan");
     if (plan->ntiles == 0) return WXPY_OK;
     if (!dev_table) return fail(WXPY_EINVAL, "null device table");
@@ -275,6 +277,7 @@ int wxpy_batch_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *s
 }
 
 int wxpy_batch_graph_launch(wxpy_batch_plan *plan, const wxpy_desc *dev_table, void *stream) {
+    TraceRange trace("wxpy_batch_graph_launch");
     if (!plan) return fail(WXPY_EINVAL, "null plan");
     if (plan->ntiles == 0) return WXPY_OK;
     if (!dev_table) return fail(WXPY_EINVAL, "null device table");
@@ -536,6 +539,7 @@ int run_shape(SynthBatch &sb, const BatchShape &shape, const DeviceProps &dp, in
 }  // namespace
 
 int batch_tune_impl(int bmin, int bmax, unsigned flags, wxpy_batch_tune_result *out) {
+    TraceRange trace("wxpy_batch_tune");
     if (bmin < 0 || bmax > 30 || bmin > bmax) return fail(WXPY_EINVAL, "bucket range must be within 0..30");
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);

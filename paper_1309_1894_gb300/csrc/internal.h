@@ -107,6 +107,9 @@ cudaError_t launch_segmented(const wxpy_desc *dev_table, const TileRec *tiles, i
                              unsigned *status, const BatchShape &shape, int sm_count,
                              cudaStream_t s);
 
+// api.cu: NVTX ranges on (WXPY_NVTX=1), read once; see trace.h.
+bool trace_enabled();
+
 // tune.cu: loads $WXPY_TUNE_CACHE once per process (errors ignored).
 void autoload_tune_cache();
 

@@ -42,6 +42,7 @@
 #include "fp64_mul.cuh"
 #include "gen.cuh"
 #include "internal.h"
+#include "trace.h"
 
 namespace wx {
 namespace {
@@ -331,6 +332,7 @@ void retire_slot(wxpy_server *sv, Slot &s, Clock::time_point now, int error) {
 // Launches the requests in `batch` on slot s.  Caller does NOT hold the lock;
 // the requests are already marked running.  Returns a cudaError_t.
 cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> &batch) {
+    TraceRange trace("wxpy_server_batch");
     cudaError_t e = cudaSuccess;
     if (sv->cfg.mode == WXPY_SERVE_SERIAL) {
         // Baseline: the same requests, launched call by call (three launches

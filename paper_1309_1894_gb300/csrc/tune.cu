@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace wx {
 namespace {
@@ -132,6 +133,7 @@ struct Candidate {
 }  // namespace
 
 int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
+    TraceRange trace("wxpy_tune");
     if (n <= 0) return fail(WXPY_EINVAL, "tune needs n > 0");
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace wx {
 namespace {
@@ -195,6 +196,7 @@ int tune_class(int cls, int64_t n, VScratch &sc, wxpy_vecops_tune_result *res) {
 }
 
 int vtune_impl(int64_t n, wxpy_vecops_tune_result *results) {
+    TraceRange trace("wxpy_vecops_tune");
     if (n <= 0) return fail(WXPY_EINVAL, "vector tune needs n > 0");
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);

@@ -108,3 +108,34 @@ def test_tuned_sweep_parity():
                 assert ok, f"n={n} off={off}: {msg}"
                 for g in (gx, gy, gw):
                     g.check()
+
+
+def test_traced_paths_run_with_nvtx_on():
+    """With WXPY_NVTX=1 (ranges around the searches, batched launches and
+    server batches) the traced paths still run and give the oracle's bits.
+    A subprocess, since the setting is read once per process."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch
+import oracle, paper_1309_1894_gb300 as wx
+from paper_1309_1894_gb300 import synth
+wx.wxpy_tune(1 << 16, wx.TUNE_QUICK)
+n = (1 << 16) + 3
+alpha, xh, yh = synth.vectors(synth.BASE_SEED + 5, n)
+x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+w = torch.empty_like(x)
+table = wx.desc_table([n], [alpha], [x.data_ptr()], [y.data_ptr()], [w.data_ptr()])
+plan = wx.BatchPlan(table)
+plan.launch(wx.table_to_device(table))
+torch.cuda.synchronize()
+assert np.array_equal(w.cpu().numpy().view(np.uint64), oracle.wxpy(alpha, xh, yh).view(np.uint64))
+wx.wxpy_vecops_tune(1 << 14)
+print("traced ok")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WXPY_NVTX="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "traced ok" in r.stdout, r.stderr[-2000:]
