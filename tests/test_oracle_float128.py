@@ -101,3 +101,40 @@ def test_mutants_fail_the_binary128_pin(checker, tmp_path, name):
         bad, _, _ = check(checker, alpha, x, y, w)
         caught = caught or bad > 0
     assert caught, f"mutant {name} passed the binary128 pin"
+
+
+def test_sibling_oracle_against_binary128(checker):
+    """The sibling oracle (vecops_oracle.c), two million cases per operation,
+    each step recomputed exactly in binary128 and rounded once."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L = checker
+    L.pin_axpbypcz.restype = L.pin_maxpy.restype = L.pin_pmult.restype = ctypes.c_int64
+    L.pin_axpbypcz.argtypes = [ctypes.c_int64] + [ctypes.c_double] * 3 + [dp] * 4 + [i64p, i64p]
+    L.pin_maxpy.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp, i64p, i64p]
+    L.pin_pmult.argtypes = [ctypes.c_int64, dp, dp, dp, i64p, i64p]
+    n = 500_000
+    c, s = ctypes.c_int64(), ctypes.c_int64()
+    for k, (al, be, ga) in enumerate(((0.75, -1.25, 3.0), (1.0, 1.0, 1.0),
+                                     (2.0 ** -20, 2.0 ** 20, -0.5), (1.5, 0.1, -7.0))):
+        x, y = cases(3000 + k, n, spread=20)
+        z, _ = cases(3100 + k, n, spread=20)
+        out = oracle.axpbypcz(al, be, ga, x, y, z)
+        bad = L.pin_axpbypcz(n, al, be, ga, _p(x), _p(y), _p(z), _p(out), ctypes.byref(c),
+                             ctypes.byref(s))
+        # wide coefficient scales (2^-20 against 2^20) leave more exponent gaps
+        # beyond binary128's exact range: a lower share is checkable there
+        assert bad == 0 and c.value >= 0.8 * n, (k, bad, c.value)
+    for m in (1, 3, 8):
+        xs = [cases(3200 + 10 * m + j, n, spread=20)[0] for j in range(m)]
+        y, _ = cases(3300 + m, n, spread=20)
+        a = np.array([0.5, -3.0, 1.0 + 2.0 ** -52, 0.25, 7.0, -0.125, 1.5, 2.0][:m])
+        out = oracle.maxpy(a, xs, y)
+        packed = np.ascontiguousarray(np.concatenate(xs))
+        bad = L.pin_maxpy(n, m, _p(a), _p(packed), _p(y), _p(out), ctypes.byref(c),
+                          ctypes.byref(s))
+        assert bad == 0 and c.value >= 0.95 * n, (m, bad, c.value)
+    x, y = cases(3400, 2 * n, spread=200)
+    out = oracle.pmult(x, y)
+    bad = L.pin_pmult(2 * n, _p(x), _p(y), _p(out), ctypes.byref(c), ctypes.byref(s))
+    assert bad == 0 and c.value >= 0.95 * 2 * n, (bad, c.value)
