@@ -114,6 +114,7 @@ def load_vec_library(path: str) -> ctypes.CDLL:
     L = ctypes.CDLL(path)
     i64, d = ctypes.c_int64, ctypes.c_double
     for name, args in (("oracle_axpy", [i64, d, dp, dp]), ("oracle_aypx", [i64, d, dp, dp]),
+                       ("oracle_axpby", [i64, d, d, dp, dp]),
                        ("oracle_axpbypcz", [i64, d, d, d, dp, dp, dp]),
                        ("oracle_maxpy", [i64, ctypes.c_int, dp, ctypes.POINTER(dp), dp]),
                        ("oracle_pmult", [i64, dp, dp, dp])):
@@ -153,6 +154,15 @@ def aypx(alpha, x, y, library=None):
     L = library or vec_lib()
     _vcheck(L.oracle_aypx(out.shape[0], float(alpha), _dptr(np.ascontiguousarray(x)), _dptr(out)),
             "oracle_aypx")
+    return out
+
+
+def axpby(alpha, beta, x, y, library=None):
+    """A new array: RN(RN(alpha*x) + RN(beta*y)) (PETSc VecAXPBY on a copy of y)."""
+    out = np.array(y, dtype=np.float64, copy=True)
+    L = library or vec_lib()
+    _vcheck(L.oracle_axpby(out.shape[0], float(alpha), float(beta),
+                           _dptr(np.ascontiguousarray(x)), _dptr(out)), "oracle_axpby")
     return out
 
 

@@ -13,6 +13,7 @@
  *
  *   axpy:      y[i] = RN(RN(alpha*x[i]) + y[i])
  *   aypx:      y[i] = RN(x[i] + RN(alpha*y[i]))
+ *   axpby:     y[i] = RN(RN(alpha*x[i]) + RN(beta*y[i]))
  *   axpbypcz:  z[i] = RN(RN(RN(alpha*x[i]) + RN(beta*y[i])) + RN(gamma*z[i]))
  *   maxpy:     y[i] = RN(... RN(RN(y[i] + RN(a[0]*x0[i])) + RN(a[1]*x1[i])) ...
  *                        + RN(a[m-1]*x_{m-1}[i]))       (terms added in order j)
@@ -52,6 +53,20 @@ int oracle_aypx(int64_t n, double alpha, const double *x, double *y)
     for (i = 0; i < n; ++i) {
         double prod = alpha * y[i];
         double sum = x[i] + prod;
+        y[i] = sum;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_axpby(int64_t n, double alpha, double beta, const double *x, double *y)
+{
+    int64_t i;
+    if (n < 0 || (n > 0 && (!x || !y)))
+        return ORACLE_BAD_ARG;
+    for (i = 0; i < n; ++i) {
+        double ax = alpha * x[i];
+        double by = beta * y[i];
+        double sum = ax + by;
         y[i] = sum;
     }
     return ORACLE_OK;

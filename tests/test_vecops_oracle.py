@@ -47,6 +47,15 @@ def check_aypx(L):
     return None
 
 
+def check_axpby(L):
+    x, y, _, _ = inputs(7, 400)
+    for (a, b) in ((0.75, -1.25), (1.0, 1.0), (2.0 ** -40, 2.0 ** 40), (-3.0, 0.5)):
+        want = [A(E(a, float(p)), E(b, float(q))) for p, q in zip(x, y)]
+        if not same(oracle.axpby(a, b, x, y, library=L), want):
+            return f"axpby {a},{b}"
+    return None
+
+
 def check_axpbypcz(L):
     x, y, z, _ = inputs(3, 400)
     for (a, b, c) in ((0.75, -1.25, 3.0), (1.0, 1.0, 1.0), (2.0 ** -40, 2.0 ** 40, -0.5)):
@@ -104,6 +113,16 @@ def check_closed_forms(L):
         acc = oracle.axpy(a_j, x_j, acc, library=L)
     if not np.array_equal(oracle.maxpy(al, xs, y, library=L).view(np.uint64), acc.view(np.uint64)):
         return "maxpy vs successive axpy"
+    # axpby with beta = 1 is axpy (RN(1*y) = y); axpby with alpha = 0 is RN(beta*y) for
+    # nonzero products
+    if not np.array_equal(oracle.axpby(0.75, 1.0, x, y, library=L).view(np.uint64),
+                          oracle.axpy(0.75, x, y, library=L).view(np.uint64)):
+        return "axpby beta=1 vs axpy"
+    got = oracle.axpby(0.0, -2.5, x, y, library=L)
+    want = np.array([E(-2.5, float(v)) for v in y])
+    keep = want != 0.0
+    if not np.array_equal(got[keep].view(np.uint64), want[keep].view(np.uint64)):
+        return "axpby alpha=0"
     # axpy agrees with the wxpy oracle (two independent implementations)
     if not np.array_equal(oracle.axpy(0.75, x, y, library=L).view(np.uint64),
                           oracle.wxpy(0.75, x, y).view(np.uint64)):
@@ -111,7 +130,8 @@ def check_closed_forms(L):
     return None
 
 
-CHECKS = [check_axpy, check_aypx, check_axpbypcz, check_maxpy, check_pmult, check_closed_forms]
+CHECKS = [check_axpy, check_aypx, check_axpby, check_axpbypcz, check_maxpy, check_pmult,
+          check_closed_forms]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
@@ -127,6 +147,8 @@ MUTANTS = {
     "aypx_swapped": ("double prod = alpha * y[i];\n        double sum = x[i] + prod;",
                      "double prod = alpha * x[i];\n        double sum = y[i] + prod;"),
     "pmult_square": ("double prod = x[i] * y[i];", "double prod = x[i] * x[i];"),
+    "axpby_beta_on_x": ("        double by = beta * y[i];\n        double sum = ax + by;",
+                        "        double by = beta * x[i];\n        double sum = ax + by;"),
     "maxpy_alpha0": ("double prod = alpha[j] * x[j][i];", "double prod = alpha[0] * x[j][i];"),
     "maxpy_drops_last": ("        for (j = 0; j < m; ++j) {\n            double prod",
                          "        for (j = 0; j + 1 < m; ++j) {\n            double prod"),
