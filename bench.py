@@ -687,6 +687,7 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
     out = [row("axpy", 24 * n, timed(lambda: wx.wxpy_axpy(0.5, v[0], v[1]))),
            row("aypx", 24 * n, timed(lambda: wx.wxpy_aypx(0.5, v[0], v[1]))),
            row("pointwise_mult", 24 * n, timed(lambda: wx.wxpy_pointwise_mult(v[0], v[1], v[2]))),
+           row("axpby", 24 * n, timed(lambda: wx.wxpy_axpby(0.5, -0.25, v[0], v[1]))),
            row("axpbypcz", 32 * n, timed(axpbypcz))]
     for m in (1, 2, 4, 8):
         out.append(row(f"maxpy_m{m}", 8 * (m + 2) * n, timed(maxpy(m))))

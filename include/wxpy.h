@@ -212,12 +212,13 @@ int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
  *
  *   wxpy_axpy:           y[i] = RN(RN(alpha*x[i]) + y[i])         (VecAXPY; = wxpy into y)
  *   wxpy_aypx:           y[i] = RN(x[i] + RN(alpha*y[i]))         (VecAYPX; = wxpy(alpha, y, x) into y)
+ *   wxpy_axpby:          y[i] = RN(RN(alpha*x[i]) + RN(beta*y[i]))   (VecAXPBY)
  *   wxpy_axpbypcz:       z[i] = RN(RN(RN(alpha*x[i]) + RN(beta*y[i])) + RN(gamma*z[i]))
  *   wxpy_maxpy:          y[i] = RN(..RN(RN(y[i] + RN(a[0]*x[0][i])) + RN(a[1]*x[1][i])).. + RN(a[m-1]*x[m-1][i]))
  *   wxpy_pointwise_mult: w[i] = RN(x[i]*y[i])                     (VecPointwiseMult)
  *
  * axpy and aypx run the tuned wxpy() variants.  When all pointers share their
- * offset mod 32 bytes, axpbypcz and maxpy stream their inputs through a
+ * offset mod 32 bytes, axpby, axpbypcz and maxpy stream their inputs through a
  * shared-memory ring filled by bulk asynchronous copies (one producer warp,
  * eight consumer warps per block, persistent grid; see wxpy_vecops_status)
  * and pointwise_mult loads 32 bytes per thread into registers; otherwise all
@@ -226,6 +227,7 @@ int wxpy_reference(int64_t n, double alpha, const double *x, const double *y,
  * terms, in order. */
 int wxpy_axpy(int64_t n, double alpha, const double *x, double *y, void *stream);
 int wxpy_aypx(int64_t n, double alpha, const double *x, double *y, void *stream);
+int wxpy_axpby(int64_t n, double alpha, double beta, const double *x, double *y, void *stream);
 int wxpy_axpbypcz(int64_t n, double alpha, double beta, double gamma, const double *x,
                   const double *y, double *z, void *stream);
 int wxpy_maxpy(int64_t n, int m, const double *alpha, const double *const *x, double *y,
@@ -239,7 +241,7 @@ int wxpy_pointwise_mult(int64_t n, const double *x, const double *y, double *w, 
  * the fraction, in sixteenths, of each warp's loop iterations whose products
  * run there (0..16).  -1 in either leaves that part to the operation's
  * searched split (wxpy_vecops_tune) or, when it has none, its default (sums
- * in FP64; products 14/16 for axpbypcz and for maxpy groups of 2 terms,
+ * in FP64; products 12/16 for axpby, 14/16 for axpbypcz and for maxpy groups of 2 terms,
  * 16/16 for groups of 3..8, 4/16 for pointwise_mult; a maxpy group of one
  * term runs as wxpy() and its tuned variant).  The bits of every result are
  * the same under every split; only the speed differs.  Process-wide, read at
@@ -251,7 +253,8 @@ int wxpy_vecops_pipes(int add_offload, int mul_sixteenths);
 #define WXPY_VEC_AXPBYPCZ 0 /* axpbypcz */
 /* 1 .. 7: a maxpy launch group of (class + 1) terms, 2 .. 8 */
 #define WXPY_VEC_PMULT 8    /* pointwise_mult */
-#define WXPY_VEC_CLASSES 9
+#define WXPY_VEC_AXPBY 9    /* axpby (its one sum: add offload 1 and 2 both move it) */
+#define WXPY_VEC_CLASSES 10
 
 typedef struct wxpy_vecops_tune_result {
     int32_t op_class;       /* WXPY_VEC_* */

@@ -73,8 +73,8 @@ class TuneResult(ctypes.Structure):
 TUNE_ALIGN16, TUNE_ALIGN8, TUNE_XY, TUNE_WALIAS, TUNE_QUICK, TUNE_RESIDENT = 1, 2, 4, 8, 16, 32
 
 # sibling-kernel classes of the pipe-split search (1 .. 7: maxpy groups of 2 .. 8 terms)
-VEC_AXPBYPCZ, VEC_PMULT, VEC_CLASSES = 0, 8, 9
-VEC_CLASS_NAMES = ["axpbypcz"] + [f"maxpy{m}" for m in range(2, 9)] + ["pointwise_mult"]
+VEC_AXPBYPCZ, VEC_PMULT, VEC_AXPBY, VEC_CLASSES = 0, 8, 9, 10
+VEC_CLASS_NAMES = ["axpbypcz"] + [f"maxpy{m}" for m in range(2, 9)] + ["pointwise_mult", "axpby"]
 
 
 class VecopsTuneResult(ctypes.Structure):
@@ -136,6 +136,7 @@ SIGNATURES = {
     "wxpy_maxpy": (_INT, [_I64, _INT, ctypes.POINTER(_D), ctypes.POINTER(_P), _P, _P]),
     "wxpy_pointwise_mult": (_INT, [_I64, _P, _P, _P, _P]),
     "wxpy_vecops_pipes": (_INT, [_INT, _INT]),
+    "wxpy_axpby": (_INT, [_I64, _D, _D, _P, _P, _P]),
     "wxpy_vecops_status": (_INT, []),
     "wxpy_reduce_workspace_bytes": (_I64, [_I64]),
     "wxpy_norm2": (_INT, [_I64, _D, _P, _P, _P, _P, _P, _I64, _P]),
@@ -310,6 +311,16 @@ def wxpy_aypx(alpha: float, x, y, stream=None):
     if n != ny:
         raise ValueError("length mismatch")
     check(lib().wxpy_aypx(n, float(alpha), px, py, _stream_handle(stream)), "wxpy_aypx")
+    return y
+
+
+def wxpy_axpby(alpha: float, beta: float, x, y, stream=None):
+    """y <- alpha*x + beta*y in place (VecAXPBY)."""
+    n, px = _vec(x, "x")
+    ny, py = _vec(y, "y")
+    if n != ny:
+        raise ValueError("length mismatch")
+    check(lib().wxpy_axpby(n, alpha, beta, px, py, _stream_handle(stream)), "wxpy_axpby")
     return y
 
 

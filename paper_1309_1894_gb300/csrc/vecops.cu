@@ -6,6 +6,7 @@
 // binary64, left to right, no fused multiply-add):
 //   axpy:      y = RN(RN(alpha*x) + y)                       = wxpy(alpha, x, y) into y
 //   aypx:      y = RN(x + RN(alpha*y)) = RN(RN(alpha*y) + x) = wxpy(alpha, y, x) into y
+//   axpby:     y = RN(RN(alpha*x) + RN(beta*y))
 //   axpbypcz:  z = RN(RN(RN(alpha*x) + RN(beta*y)) + RN(gamma*z))
 //   maxpy:     y = RN(... RN(RN(y + RN(a0*x0)) + RN(a1*x1)) ... + RN(a_{m-1}*x_{m-1}))
 //   pmult:     w = RN(x*y)
@@ -91,6 +92,18 @@ __device__ __forceinline__ void products(const Coefs &c, const double (&e)[NIN],
         for (int j = 0; j < K; ++j) p[j] = double_of(b[j]);
     }
 }
+
+template <int OFF>
+struct AxpbyOp {
+    static constexpr int kIn = 2;  // x, y
+    static constexpr bool kStaged = true;
+    template <int PM>
+    __device__ __forceinline__ static double apply(const Coefs &c, const double (&e)[kIn]) {
+        double p[2];
+        products<PM>(c, e, p);
+        return add_sel<OFF>(p[0], p[1], 1);
+    }
+};
 
 template <int OFF>
 struct AxpbypczOp {
@@ -483,7 +496,7 @@ int launch_ew(const double *const *in, double *out, int64_t n, const double *coe
 // either leaves the operation's searched split, else its default (below).
 std::atomic<int> g_vec_add{-1};
 std::atomic<int> g_vec_mul{-1};
-std::atomic<int> g_vec_tuned[WXPY_VEC_CLASSES] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+std::atomic<int> g_vec_tuned[WXPY_VEC_CLASSES] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 
 using Pipes = VecPipes;
 
@@ -511,13 +524,14 @@ int maxpy_group(int64_t n, const double *alpha, const double *const *in, Pipes p
 // them; the product share that balanced the FP64 and ALU pipelines best).
 VecPipes vecops_default(int cls) {
     if (cls == WXPY_VEC_AXPBYPCZ) return {0, 14};
+    if (cls == WXPY_VEC_AXPBY) return {0, 10};
     if (cls == WXPY_VEC_PMULT) return {0, 4};
     return {0, cls + 1 == 2 ? 14 : 16};  // maxpy with cls + 1 terms
 }
 
 int vecops_inputs(int cls) {
     if (cls == WXPY_VEC_AXPBYPCZ) return 3;
-    if (cls == WXPY_VEC_PMULT) return 2;
+    if (cls == WXPY_VEC_PMULT || cls == WXPY_VEC_AXPBY) return 2;
     return cls + 2;  // y and cls + 1 x vectors
 }
 
@@ -545,6 +559,11 @@ int vecops_run(int cls, int64_t n, const double *coef, const double *const *in, 
                 default: return launch_ew<AxpbypczOp<2>>(in, out, n, coef, 3, p.mul, s);
             }
         case WXPY_VEC_PMULT: return launch_ew<PmultOp>(in, out, n, nullptr, 0, p.mul, s);
+        case WXPY_VEC_AXPBY:
+            switch (p.add) {
+                case 0: return launch_ew<AxpbyOp<0>>(in, out, n, coef, 2, p.mul, s);
+                default: return launch_ew<AxpbyOp<2>>(in, out, n, coef, 2, p.mul, s);
+            }
         case 1: return maxpy_group<2>(n, coef, in, p, s);
         case 2: return maxpy_group<3>(n, coef, in, p, s);
         case 3: return maxpy_group<4>(n, coef, in, p, s);
@@ -568,6 +587,13 @@ int wxpy_axpy(int64_t n, double alpha, const double *x, double *y, void *stream)
 
 int wxpy_aypx(int64_t n, double alpha, const double *x, double *y, void *stream) {
     return wxpy(n, alpha, y, x, y, stream);
+}
+
+int wxpy_axpby(int64_t n, double alpha, double beta, const double *x, double *y, void *stream) {
+    const double *in[2] = {x, y};
+    const double coef[2] = {alpha, beta};
+    return vecops_run(WXPY_VEC_AXPBY, n, coef, in, y, pipes_for(WXPY_VEC_AXPBY),
+                      (cudaStream_t)stream);
 }
 
 int wxpy_axpbypcz(int64_t n, double alpha, double beta, double gamma, const double *x,

@@ -72,6 +72,14 @@ struct ClassCall {
     double *restore;  // nullptr: out-of-place (pointwise_mult)
 };
 
+// The in-place output of a class (an input too): z of axpbypcz, y of axpby
+// and of maxpy; pointwise_mult writes a separate vector.
+double *inplace_out(int cls, VScratch &sc) {
+    if (cls == WXPY_VEC_AXPBYPCZ) return sc.v[2];
+    if (cls == WXPY_VEC_AXPBY) return sc.v[1];
+    return sc.v[0];
+}
+
 ClassCall class_call(int cls, VScratch &sc) {
     ClassCall c{};
     c.cls = cls;
@@ -81,7 +89,7 @@ ClassCall class_call(int cls, VScratch &sc) {
         c.out = sc.w;
         c.restore = nullptr;
     } else {
-        c.out = cls == WXPY_VEC_AXPBYPCZ ? sc.v[2] : sc.v[0];  // z, or y of maxpy
+        c.out = inplace_out(cls, sc);
         c.restore = c.out;
     }
     return c;
@@ -222,7 +230,7 @@ int vtune_impl(int64_t n, wxpy_vecops_tune_result *results) {
             return st;
     for (int cls = 0; cls < WXPY_VEC_CLASSES; ++cls) {
         // pristine copy of the in-place output of this class
-        double *out = cls == WXPY_VEC_AXPBYPCZ ? sc.v[2] : sc.v[0];
+        double *out = inplace_out(cls, sc);
         e = cudaMemcpyAsync(sc.pristine, out, bytes, cudaMemcpyDeviceToDevice, sc.s);
         if (e != cudaSuccess) return fail_cuda(e, "vector tuner copy");
         if ((st = tune_class(cls, n, sc, results ? &results[cls] : nullptr)) != WXPY_OK) return st;

@@ -123,6 +123,25 @@ int64_t pin_axpbypcz(int64_t n, double al, double be, double ga, const double *x
     return bad;
 }
 
+/* y_out[i] == RN(RN(al*x) + RN(be*y)) */
+int64_t pin_axpby(int64_t n, double al, double be, const double *x, const double *y,
+                  const double *y_out, int64_t *checked, int64_t *skipped) {
+    int64_t bad = 0, ok = 0, skip = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int s = 0;
+        const double r = rn_sum(rn_prod(al, x[i], &s), rn_prod(be, y[i], &s), &s);
+        if (s) {
+            ++skip;
+            continue;
+        }
+        bad += !same_bits(r, y_out[i]);
+        ++ok;
+    }
+    *checked = ok;
+    *skipped = skip;
+    return bad;
+}
+
 /* y_out[i] == y[i] + a[0]*x[0][i] + ... in order, every step rounded; the x
  * vectors are packed one after another (m blocks of n). */
 int64_t pin_maxpy(int64_t n, int m, const double *a, const double *xs, const double *y,

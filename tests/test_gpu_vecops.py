@@ -60,6 +60,22 @@ def test_axpbypcz(split, offs, special):
             g.check()
 
 
+@pytest.mark.parametrize("special", [False, True])
+@pytest.mark.parametrize("split", SPLITS)
+@pytest.mark.parametrize("offs", [(0, 0), (8, 8), (0, 24)])
+def test_axpby(split, offs, special):
+    wx.wxpy_vecops_pipes(*split)
+    for n in SIZES:
+        xh, yh = (vals(20 * n + k, n, special) for k in range(2))
+        gx, gy = Guarded(n, offs[0]).set(xh), Guarded(n, offs[1]).set(yh)
+        a, b = -0.625, 1.5 + 2.0 ** -51
+        wx.wxpy_axpby(a, b, gx.t, gy.t)
+        torch.cuda.synchronize()
+        assert same(gy.t, oracle.axpby(a, b, xh, yh)), (n, offs)
+        for g in (gx, gy):
+            g.check()
+
+
 @pytest.mark.parametrize("split", SPLITS)
 @pytest.mark.parametrize("m", [0, 1, 3, 8, 9, 17])
 def test_maxpy(split, m):

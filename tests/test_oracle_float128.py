@@ -134,6 +134,15 @@ def test_sibling_oracle_against_binary128(checker):
         bad = L.pin_maxpy(n, m, _p(a), _p(packed), _p(y), _p(out), ctypes.byref(c),
                           ctypes.byref(s))
         assert bad == 0 and c.value >= 0.95 * n, (m, bad, c.value)
+    L.pin_axpby.restype = ctypes.c_int64
+    L.pin_axpby.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                            i64p, i64p]
+    for k, (al, be) in enumerate(((0.75, -1.25), (1.0, 1.0), (-3.0, 2.0 ** -30),
+                                  (0.1, 1.0 + 2.0 ** -52))):
+        x, y = cases(3500 + k, n, spread=20)
+        out = oracle.axpby(al, be, x, y)
+        bad = L.pin_axpby(n, al, be, _p(x), _p(y), _p(out), ctypes.byref(c), ctypes.byref(s))
+        assert bad == 0 and c.value >= 0.9 * n, (k, bad, c.value)
     x, y = cases(3400, 2 * n, spread=200)
     out = oracle.pmult(x, y)
     bad = L.pin_pmult(2 * n, _p(x), _p(y), _p(out), ctypes.byref(c), ctypes.byref(s))

@@ -91,7 +91,7 @@ def test_load_vecops_section(tmp_path):
     assert wx.wxpy_tune_get(4) == 11
 
 
-@pytest.mark.parametrize("entry", [{"class": 9, "add_offload": 0, "mul_sixteenths": 2},
+@pytest.mark.parametrize("entry", [{"class": wx.VEC_CLASSES, "add_offload": 0, "mul_sixteenths": 2},
                                    {"class": 1, "add_offload": 3, "mul_sixteenths": 2},
                                    {"class": 1, "add_offload": 0, "mul_sixteenths": 17},
                                    {"class": 1, "add_offload": 0}])
