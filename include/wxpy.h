@@ -315,9 +315,12 @@ int wxpy_vecops_status(void);
  * wxpy_reduce_workspace_bytes(n) bytes, 16-byte aligned, disjoint from the
  * vectors and result, owned by the caller; the call overwrites it, so calls in
  * flight at the same time need separate workspaces.  Nothing is allocated.
- * 32-byte co-aligned pointers take coalesced 32-byte accesses; others element
- * ones (same bits).  Errors: WXPY_EINVAL (bad argument, workspace too small),
- * WXPY_EOVERLAP, WXPY_ECUDA. */
+ * When x, y, w (and z) are all 32-byte aligned, the inputs stream through
+ * shared memory by bulk asynchronous copies (a producer warp and eight
+ * consumer warps per block, every wait bounded; see wxpy_reduce_status);
+ * otherwise every element is read and written on its own (same bits).
+ * Errors: WXPY_EINVAL (bad argument, workspace too small), WXPY_EOVERLAP,
+ * WXPY_ECUDA. */
 int64_t wxpy_reduce_workspace_bytes(int64_t n);
 int wxpy_norm2(int64_t n, double alpha, const double *x, const double *y, double *w,
                double *result, void *workspace, int64_t workspace_bytes, void *stream);
@@ -330,6 +333,20 @@ int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *
  * instead of FP64 instructions (a rotation over blocks and tiles): 0..16, -1
  * the default.  Same bits either way.  Process-wide. */
 int wxpy_reduce_pipes(int mul_sixteenths);
+
+/* The kernel of wxpy_norm2 / wxpy_dot for 32-byte co-aligned pointers
+ * (other alignments always take the element path): 0 register-loaded (a
+ * block of 256 threads per tile, 32-byte loads into registers); 1, 2, 3
+ * staged through a shared-memory ring of bulk copies with (ring stages,
+ * resident blocks per SM) = (4, 2), (3, 3), (2, 3); -1 the default.  Same
+ * bits for every variant.  Process-wide. */
+int wxpy_reduce_variant(int variant);
+
+/* Synchronises the current device, then returns WXPY_ETIMEOUT (and clears
+ * the record) if a bounded wait of a staged reduction launched since the last
+ * call ran out -- its w and result are then not to be used -- else WXPY_OK.
+ * WXPY_ECUDA if the synchronisation fails. */
+int wxpy_reduce_status(void);
 
 /* ---- batched launch: many independent problems in one launch ----------------- */
 
@@ -675,6 +692,13 @@ int wxpy_debug_inject_launch_error(int cuda_error, int count);
  * runs out and wxpy_vecops_status() reports WXPY_ETIMEOUT; no copy is left in
  * flight.  -1 (the default) turns it off.  Process-wide. */
 int wxpy_debug_vecops_drop_tile(int64_t tile);
+
+/* Staged reductions launched after this call stop issuing copies before
+ * chunk `chunk` (1024 elements; chunk c of tile t is 8t + c), so the owning
+ * block's consumers' bounded waits run out and wxpy_reduce_status() reports
+ * WXPY_ETIMEOUT; no copy is left in flight.  -1 (the default) turns it off.
+ * Process-wide. */
+int wxpy_debug_reduce_drop_chunk(int64_t chunk);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,9 @@ SIGNATURES = {
     "wxpy_norm2": (_INT, [_I64, _D, _P, _P, _P, _P, _P, _I64, _P]),
     "wxpy_dot": (_INT, [_I64, _D, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "wxpy_reduce_pipes": (_INT, [_INT]),
+    "wxpy_reduce_status": (_INT, []),
+    "wxpy_reduce_variant": (_INT, [_INT]),
+    "wxpy_debug_reduce_drop_chunk": (_INT, [_I64]),
     "wxpy_vecops_tune": (_INT, [_I64, ctypes.POINTER(VecopsTuneResult)]),
     "wxpy_vecops_tuned_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     "wxpy_vecops_tuned_set": (_INT, [_INT, _INT, _INT]),
@@ -411,6 +414,21 @@ def wxpy_dot(alpha: float, x, y, z, w=None, result=None, workspace=None, stream=
 
 def wxpy_reduce_pipes(mul_sixteenths: int = -1) -> None:
     check(lib().wxpy_reduce_pipes(mul_sixteenths), "wxpy_reduce_pipes")
+
+
+def wxpy_reduce_variant(variant: int = -1) -> None:
+    """Kernel of the fused reductions for co-aligned pointers: 0 register-
+    loaded, 1..3 staged shapes, -1 the default (same bits for all)."""
+    check(lib().wxpy_reduce_variant(variant), "wxpy_reduce_variant")
+
+
+def wxpy_reduce_status() -> None:
+    """Raises WxpyError(WXPY_ETIMEOUT) if a staged reduction's bounded wait ran out."""
+    check(lib().wxpy_reduce_status(), "wxpy_reduce_status")
+
+
+def wxpy_debug_reduce_drop_chunk(chunk: int) -> None:
+    check(lib().wxpy_debug_reduce_drop_chunk(chunk), "wxpy_debug_reduce_drop_chunk")
 
 
 def wxpy_vecops_pipes(add_offload: int = -1, mul_sixteenths: int = -1) -> None:

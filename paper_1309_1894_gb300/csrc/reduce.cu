@@ -9,15 +9,38 @@
 // (e[i] = RN(e[i] + e[i + s]) for s = T/2, ..., 1, +0 past n); the tile sums,
 // padded with +0 to a power of two, are summed by the same tree.
 //
-// Mapping.  A block of 256 threads takes a tile; thread t owns the 32-byte
-// vectors at element 1024k + 4t (k = 0..7), so element i = 1024k + 4t + q has
-// bits 12..10 = k, 9..7 = warp, 6..2 = lane, 1..0 = q.  The halving tree
-// reduces bits from the top down, and each level is done where its two
-// operands live: bits 12..10 inside the thread (k and k + 4 as they arrive,
-// then k + 2, k + 1), bits 9..7 across warps through shared memory, bits 6..2
-// by warp shuffles, bits 1..0 inside lane 0.  Every load and store is a
-// coalesced 32-byte vector.  The tile sums go to a workspace; the last block to
-// finish (an atomic ticket, no waiting) sums them with the same tree.
+// Staged path (x, y, w and z 32-byte co-aligned).  A persistent grid; each
+// block owns tiles blockIdx.x, blockIdx.x + gridDim.x, ...  One producer warp
+// copies a tile as eight 1024-element chunks of every input into a shared-
+// memory ring (bulk asynchronous copies completed on "full" mbarriers; a stage
+// is reused once all eight consumer warps have released it on its "empty"
+// barrier).  Chunk c of a tile holds indices 1024c .. 1024c + 1023, and
+// consumer thread (warp v, lane l) takes the 16-byte pairs 128v + 64h + 2l
+// (h = 0, 1) of every chunk, so element i = 1024c + 128v + 64h + 2l + q has
+// bits 12..10 = c, 9..7 = v, 6 = h, 5..1 = l, 0 = q; every shared-memory and
+// global access of a warp is 512 contiguous bytes.  The halving tree reduces
+// bits from the top down:
+//   - bits 12..10 in the thread: the producer copies the chunks in bit-
+//     reversed order (0, 4, 2, 6, 1, 5, 3, 7), so each tree node is complete
+//     as soon as its second half arrives and three partial vectors suffice;
+//   - bits 9..7 across warps: every warp writes its four node values to one
+//     of two exchange slots (an mbarrier pair per slot, so no warp waits for
+//     the others except through a bounded wait), and one warp, rotating with
+//     the tile, finishes the tile: bits 9..7, then bit 6 in the thread,
+//     bits 5..1 by warp shuffles, bit 0 in lane 0.
+// The last tile, when n is not a multiple of 8192, is read from global memory
+// by the same threads in the same order, +0 past n.  Loads never wait on
+// compute: the ring keeps up to S - 1 stages in flight.  Every mbarrier wait is
+// bounded (bulk.cuh); one that runs out ends the kernel and is reported by
+// wxpy_reduce_status().
+//
+// Element path (other alignments).  A block of 256 threads takes a tile;
+// thread t owns elements 1024k + 4t + q (k = 0..7, q = 0..3): bits 12..10 in
+// the thread, 9..7 across warps through shared memory, 6..2 by shuffles, 1..0
+// in lane 0, each element read and written on its own.
+//
+// Either way the tile sums go to a workspace, and the last block to finish
+// (an atomic ticket, no waiting) sums them with the same tree.
 //
 // Pipes: per element two products (alpha*x and the term) and, on average, two
 // sums (the update's and one tree level).  A share of the tiles (mul_sixteenths,
@@ -32,6 +55,7 @@
 #include <atomic>
 #include <cstring>
 
+#include "bulk.cuh"
 #include "fp64_emu.cuh"
 #include "fp64_mul.cuh"
 #include "internal.h"
@@ -53,6 +77,7 @@ struct ReduceArgs {
     double alpha;
     MulCoef ca;
     int mul_sixteenths;
+    int64_t drop_chunk;  // staged path: the producer stops before this chunk (-1: never)
 };
 
 __device__ __forceinline__ uint64_t bits_of(double v) { return (uint64_t)__double_as_longlong(v); }
@@ -76,7 +101,8 @@ __device__ __forceinline__ void element(const ReduceArgs &a, double x, double y,
     }
 }
 
-// Coherent evict-first loads: w may be one of the inputs.
+
+// Coherent evict-first 32-byte accesses: w may be one of the inputs.
 __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
     asm volatile("ld.global.cs.v4.f64 {%0,%1,%2,%3}, [%4];"
                  : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
@@ -89,14 +115,13 @@ __device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
                  : "memory");
 }
 
-// Terms of the four elements of vector k of this thread (base = its first
-// index in the vector); w stored.  VEC: whole, 32-byte co-aligned vector;
-// else element by element with bounds (ragged tile, or unaligned pointers),
+// Terms of the four elements base .. base + 3; w stored.  VEC: one 32-byte
+// co-aligned vector of every operand; else element by element with bounds,
 // +0 terms past n.
 template <int KIND, bool EMU, bool VEC>
 __device__ __forceinline__ void vector_terms(const ReduceArgs &a, int64_t base, double (&t)[4]) {
-    double x[4], y[4], z[4], w[4];
     if constexpr (VEC) {
+        double x[4], y[4], z[4], w[4];
         ld4(a.x + base, x);
         ld4(a.y + base, y);
         if constexpr (KIND == 1) ld4(a.z + base, z);
@@ -186,7 +211,24 @@ __device__ void final_tree(const ReduceArgs &a) {
     if (t == 0) *a.result = __ldcg(a.partial);
 }
 
-// Four resident blocks (64 registers): measured 4-5 % faster than three.
+// The last block to finish (after every tile sum of this grid is written)
+// sums the tile sums.  All threads of the block take part.
+__device__ __forceinline__ void finish_grid(const ReduceArgs &a, bool &last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        final_tree(a);
+    }
+}
+
+// Register-loaded path: four resident blocks (64 registers), measured 4-5 %
+// faster than three.  VEC: full tiles by 32-byte vectors (co-aligned
+// pointers); the last tile, and every tile otherwise, element by element.
 template <int KIND, bool VEC>
 __global__ void __launch_bounds__(kThreads, 4) wxpy_reduce_kernel(const ReduceArgs a) {
     __shared__ double red[kThreads][4];
@@ -201,16 +243,312 @@ __global__ void __launch_bounds__(kThreads, 4) wxpy_reduce_kernel(const ReduceAr
         if (threadIdx.x == 0) a.partial[tile] = s;
         slot = (slot + 1u) & 15u;
     }
-    // the last block to finish sums the tile sums
-    if (threadIdx.x == 0) {
+    finish_grid(a, last);
+}
+
+// ---- staged path ---------------------------------------------------------------
+
+constexpr int kChunk = 1024;  // elements of one input per stage
+constexpr int kConsumerWarps = 8;
+constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
+
+// Bitmask of the waits that ran out (1: producer, 2: consumer, 4: exchange);
+// read and cleared by wxpy_reduce_status().
+__device__ unsigned int g_reduce_fault;
+
+template <int KIND, int S>
+struct ReduceStage {
+    static constexpr int kIn = KIND == 1 ? 3 : 2;
+    static constexpr int kStages = S;
+    static constexpr int kStageElems = kIn * kChunk;
+    static constexpr int kRingBytes = kStages * kStageElems * 8;
+    static constexpr int kExchBytes = 2 * kConsumerWarps * 32 * 4 * 8;  // two slots
+    static constexpr int kSmem = kRingBytes + kExchBytes;
+};
+
+// j-th chunk of a tile in copy order: j with its three bits reversed.
+__device__ __forceinline__ int chunk_of(int j) { return ((j & 1) << 2) | (j & 2) | ((j >> 2) & 1); }
+
+__device__ __forceinline__ void ld_shared_v2(const double *p, double &a, double &b) {
+    asm volatile("ld.shared.v2.f64 {%0,%1}, [%2];" : "=d"(a), "=d"(b) : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void st_shared_v2(double *p, double a, double b) {
+    asm volatile("st.shared.v2.f64 [%0], {%1,%2};" ::"r"(smem_addr(p)), "d"(a), "d"(b) : "memory");
+}
+
+__device__ __forceinline__ void st_global_v2_cs(double *p, double a, double b) {
+    asm volatile("st.global.cs.v2.f64 [%0], {%1,%2};" ::"l"(p), "d"(a), "d"(b) : "memory");
+}
+
+// Folds the terms of the j-th chunk (in copy order) into the three partial
+// vectors: after j = 7, acc0 holds the tree over bits 12..10.
+__device__ __forceinline__ void fold(int j, double (&acc0)[4], double (&acc1)[4], double (&acc2)[4],
+                                     const double (&e)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        switch (j) {
+            case 0: acc0[q] = e[q]; break;
+            case 1: acc0[q] = __dadd_rn(acc0[q], e[q]); break;
+            case 2: acc1[q] = e[q]; break;
+            case 3: acc0[q] = __dadd_rn(acc0[q], __dadd_rn(acc1[q], e[q])); break;
+            case 4: acc1[q] = e[q]; break;
+            case 5: acc1[q] = __dadd_rn(acc1[q], e[q]); break;
+            case 6: acc2[q] = e[q]; break;
+            default:
+                acc0[q] = __dadd_rn(acc0[q], __dadd_rn(acc1[q], __dadd_rn(acc2[q], e[q])));
+        }
+    }
+}
+
+// Terms of one staged chunk (copy position i of this block), w stored; false
+// when the wait ran out.
+template <int KIND, int S, bool EMU>
+__device__ __forceinline__ bool staged_chunk(const ReduceArgs &a, const double *ring,
+                                             uint64_t *full, uint64_t *empty, int i, double *wp,
+                                             int off, int lane, double (&e)[4]) {
+    using RS = ReduceStage<KIND, S>;
+    const int s = i % S;
+    if (!mbar_wait(smem_addr(&full[s]), (i / S) & 1)) return false;
+    const double *sb = ring + (size_t)s * RS::kStageElems + off;
+    double x[4], y[4], z[4], w[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ld_shared_v2(sb + 64 * h, x[2 * h], x[2 * h + 1]);
+        ld_shared_v2(sb + kChunk + 64 * h, y[2 * h], y[2 * h + 1]);
+        if constexpr (KIND == 1) ld_shared_v2(sb + 2 * kChunk + 64 * h, z[2 * h], z[2 * h + 1]);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(&empty[s]));  // the stage is in registers
+#pragma unroll
+    for (int q = 0; q < 4; ++q) element<KIND, EMU>(a, x[q], y[q], KIND == 1 ? z[q] : 0.0, w[q], e[q]);
+    st_global_v2_cs(wp, w[0], w[1]);
+    st_global_v2_cs(wp + 64, w[2], w[3]);
+    return true;
+}
+
+// The four node values (bits 12..10 reduced; index 2h + q) of this thread for
+// a full tile, from the ring; `i` counts the chunks this block has consumed.
+// A rolled loop over the four chunk pairs of the copy order, (0, 4), (2, 6),
+// (1, 5), (3, 7): each pair's sum is the tree's first level, and a shift of
+// the four pair sums through registers leaves them in order for the last two
+// levels, so no sum is ever predicated off.  False when a wait ran out.
+template <int KIND, int S, bool EMU>
+__device__ __forceinline__ bool staged_tile(const ReduceArgs &a, const double *ring,
+                                            uint64_t *full, uint64_t *empty, int &i, int64_t tile,
+                                            int warp, int lane, double (&v)[4]) {
+    const int off = 128 * warp + 2 * lane;
+    double r0[4], r1[4], r2[4], r3[4];
+#pragma unroll 1
+    for (int m = 0; m < 4; ++m) {
+        double e0[4], e1[4];
+        double *wp = a.w + tile * kTile + off;
+        if (!staged_chunk<KIND, S, EMU>(a, ring, full, empty, i, wp + chunk_of(2 * m) * kChunk, off,
+                                        lane, e0))
+            return false;
+        if (!staged_chunk<KIND, S, EMU>(a, ring, full, empty, i + 1,
+                                        wp + chunk_of(2 * m + 1) * kChunk, off, lane, e1))
+            return false;
+        i += 2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            r0[q] = r1[q];
+            r1[q] = r2[q];
+            r2[q] = r3[q];
+            r3[q] = __dadd_rn(e0[q], e1[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __dadd_rn(__dadd_rn(r0[q], r1[q]), __dadd_rn(r2[q], r3[q]));
+    return true;
+}
+
+// The same for the last, ragged tile, from global memory; +0 terms past n.
+template <int KIND>
+__device__ __forceinline__ void ragged_tile(const ReduceArgs &a, int64_t tile, int warp, int lane,
+                                            double (&v)[4]) {
+    const int off = 128 * warp + 2 * lane;
+    double acc1[4], acc2[4];
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+        double e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = tile * kTile + chunk_of(j) * kChunk + off + 64 * (q >> 1) + (q & 1);
+            if (i < a.n) {
+                double wi;
+                element<KIND, false>(a, a.x[i], a.y[i], KIND == 1 ? a.z[i] : 0.0, wi, e[q]);
+                a.w[i] = wi;
+            } else {
+                e[q] = 0.0;
+            }
+        }
+        fold(j, v, acc1, acc2, e);
+    }
+}
+
+// Exchange slot layout: [warp][h][lane][q], so that every access of a warp is
+// 512 contiguous bytes.
+__device__ __forceinline__ int exch_index(int warp, int h, int lane) {
+    return ((warp * 2 + h) * 32 + lane) * 2;
+}
+
+// Bits 9..7, 6, 5..1 and 0 of tile `tile` from an exchange slot, by one warp;
+// lane 0 writes the tile sum.
+__device__ __forceinline__ void finish_tile(const ReduceArgs &a, const double *xs, int64_t tile,
+                                            int lane) {
+    double r[kConsumerWarps][4];
+#pragma unroll
+    for (int v = 0; v < kConsumerWarps; ++v) {
+        ld_shared_v2(xs + exch_index(v, 0, lane), r[v][0], r[v][1]);
+        ld_shared_v2(xs + exch_index(v, 1, lane), r[v][2], r[v][3]);
+    }
+    double u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // bits 9..7: v and v + 4, v + 2, v + 1
+        const double b0 = __dadd_rn(r[0][q], r[4][q]), b1 = __dadd_rn(r[1][q], r[5][q]);
+        const double b2 = __dadd_rn(r[2][q], r[6][q]), b3 = __dadd_rn(r[3][q], r[7][q]);
+        u[q] = __dadd_rn(__dadd_rn(b0, b2), __dadd_rn(b1, b3));
+    }
+    double p[2] = {__dadd_rn(u[0], u[2]), __dadd_rn(u[1], u[3])};  // bit 6: h = 0 and 1
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) {  // bits 5..1: lanes l and l + 16, .., l + 1
+#pragma unroll
+        for (int q = 0; q < 2; ++q) p[q] = __dadd_rn(p[q], __shfl_down_sync(0xffffffffu, p[q], sh));
+    }
+    if (lane == 0) {
+        a.partial[tile] = __dadd_rn(p[0], p[1]);  // bit 0
         __threadfence();
-        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+}
+
+template <int KIND, int S, int MINB>
+__global__ void __launch_bounds__(kStagedThreads, MINB) wxpy_reduce_staged_kernel(const ReduceArgs a) {
+    using RS = ReduceStage<KIND, S>;
+    constexpr int NIN = RS::kIn;
+    extern __shared__ __align__(128) double ring[];  // [S][NIN][kChunk], then the exchange
+    double *exch = ring + (size_t)S * RS::kStageElems;  // two slots of 8 x 128 doubles
+    __shared__ __align__(8) uint64_t full[S], empty[S], xfull[2], xempty[2];
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t full_tiles = a.n / kTile;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), kConsumerWarps);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_addr(&xfull[s]), kConsumerWarps);
+            mbar_init(smem_addr(&xempty[s]), 1);
+        }
+        mbar_init_fence();
     }
     __syncthreads();
-    if (last) {
-        __threadfence();
-        final_tree(a);
+    if (warp == kConsumerWarps) {
+        if (lane == 0) {
+            const double *in[3] = {a.x, a.y, a.z};
+            const uint64_t policy = evict_first_policy();
+            bool ok = true;
+            int i = 0;
+            for (int64_t t = blockIdx.x; t < full_tiles && ok; t += gridDim.x) {
+                for (int j = 0; j < 8; ++j, ++i) {
+                    const int64_t chunk = t * 8 + chunk_of(j);
+                    if (chunk == a.drop_chunk) {
+                        t = full_tiles;  // stop issuing; the consumers' waits run out
+                        break;
+                    }
+                    const int s = i % S;
+                    if (i >= S && !mbar_wait(smem_addr(&empty[s]), ((i / S) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bar = smem_addr(&full[s]);
+                    mbar_arrive_expect_tx(bar, NIN * kChunk * 8u);
+#pragma unroll
+                    for (int k = 0; k < NIN; ++k)
+                        bulk_load(smem_addr(ring + (size_t)s * RS::kStageElems + k * kChunk),
+                                  in[k] + chunk * kChunk, kChunk * 8u, bar, policy);
+                }
+            }
+            // every issued copy lands before the block exits
+            for (int j = i > S ? i - S : 0; j < i; ++j)
+                if (!mbar_wait(smem_addr(&full[j % S]), (j / S) & 1)) ok = false;
+            if (!ok) atomicOr(&g_reduce_fault, 1u);
+        }
+    } else {
+        unsigned slot = (blockIdx.x * 7u) & 15u;  // block-uniform rotation of the pipe choice
+        int i = 0, k = 0;
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+            double v[4];
+            if (t < full_tiles) {
+                const bool ok = (int)slot < a.mul_sixteenths
+                                    ? staged_tile<KIND, S, true>(a, ring, full, empty, i, t, warp, lane, v)
+                                    : staged_tile<KIND, S, false>(a, ring, full, empty, i, t, warp, lane, v);
+                if (!ok) {
+                    if (lane == 0) atomicOr(&g_reduce_fault, 2u);
+                    break;
+                }
+            } else {
+                ragged_tile<KIND>(a, t, warp, lane, v);
+            }
+            // exchange slot k & 1: free once the tile two back was finished
+            const int xs = k & 1;
+            if (k >= 2 && !mbar_wait(smem_addr(&xempty[xs]), ((k >> 1) - 1) & 1)) {
+                if (lane == 0) atomicOr(&g_reduce_fault, 4u);
+                break;
+            }
+            double *slotp = exch + (size_t)xs * kConsumerWarps * 128;
+            st_shared_v2(slotp + exch_index(warp, 0, lane), v[0], v[1]);
+            st_shared_v2(slotp + exch_index(warp, 1, lane), v[2], v[3]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&xfull[xs]));
+            if (warp == (k & 7)) {
+                if (!mbar_wait(smem_addr(&xfull[xs]), (k >> 1) & 1)) {
+                    if (lane == 0) atomicOr(&g_reduce_fault, 4u);
+                    break;
+                }
+                finish_tile(a, slotp, t, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&xempty[xs]));
+            }
+            slot = (slot + 1u) & 15u;
+        }
     }
+    finish_grid(a, last);
+}
+
+// Per staged shape and device: the dynamic shared-memory opt-in done and the
+// resident blocks per SM (0 on failure).
+template <int KIND, int S, int MINB>
+int staged_blocks_per_sm(int device) {
+    static std::atomic<int> cached[64];
+    if (device < 0 || device >= 64) return 0;
+    int v = cached[device].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    constexpr int smem = ReduceStage<KIND, S>::kSmem;
+    if (cudaFuncSetAttribute(wxpy_reduce_staged_kernel<KIND, S, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wxpy_reduce_staged_kernel<KIND, S, MINB>,
+                                                      kStagedThreads, smem) != cudaSuccess ||
+        nb < 1)
+        return 0;
+    cached[device].store(nb, std::memory_order_relaxed);
+    return nb;
+}
+
+template <int KIND, int S, int MINB>
+cudaError_t launch_staged(const ReduceArgs &a, const DeviceProps *dp, cudaStream_t s) {
+    const int nb = staged_blocks_per_sm<KIND, S, MINB>(dp->device);
+    if (nb == 0) {
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
+    }
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)dp->sm_count * nb, a.ntiles));
+    wxpy_reduce_staged_kernel<KIND, S, MINB>
+        <<<(unsigned)grid, kStagedThreads, ReduceStage<KIND, S>::kSmem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int KIND, bool VEC>
@@ -230,6 +568,13 @@ int blocks_per_sm(int device) {
 }
 
 std::atomic<int> g_reduce_mul{-1};
+std::atomic<long long> g_reduce_drop{-1};
+std::atomic<int> g_reduce_variant{-1};
+constexpr int kReduceVariants = 4;
+// Measured on GB300 at n = 2^26 with every product in the integer pipelines
+// (GB/s of algorithmic bytes, norm2 / dot): register-loaded 4482 / 5485;
+// staged (4, 2) 3771 / 4575, (3, 3) 3822 / 4252, (2, 3) 3904 / 4851.
+constexpr int kDefaultVariant[2] = {0, 0};  // norm2, dot
 constexpr int kDefaultMulSixteenths = 16;  // measured fastest on GB300 (both operations)
 
 int64_t padded_tiles(int64_t n) {
@@ -297,14 +642,25 @@ int launch_reduce(int64_t n, double alpha, const double *x, const double *y, dou
     a.ca = mul_coef_of(ab);
     const int m = g_reduce_mul.load();
     a.mul_sixteenths = m < 0 ? kDefaultMulSixteenths : m;
+    a.drop_chunk = g_reduce_drop.load();
     uintptr_t any = (uintptr_t)x | (uintptr_t)y | (uintptr_t)w | (KIND == 1 ? (uintptr_t)z : 0);
     const bool vec = (any & 31u) == 0;
     e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return fail_cuda(e, "reduce ticket");
-    const int nb = vec ? blocks_per_sm<KIND, true>(dp->device) : blocks_per_sm<KIND, false>(dp->device);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)dp->sm_count * nb, a.ntiles));
-    if (vec) wxpy_reduce_kernel<KIND, true><<<(unsigned)grid, kThreads, 0, s>>>(a);
-    else wxpy_reduce_kernel<KIND, false><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    const int v = g_reduce_variant.load();
+    const int variant = !vec ? 0 : v < 0 ? kDefaultVariant[KIND] : v;
+    if (variant == 0) {
+        const int nb = vec ? blocks_per_sm<KIND, true>(dp->device) : blocks_per_sm<KIND, false>(dp->device);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)dp->sm_count * nb, a.ntiles));
+        if (vec) wxpy_reduce_kernel<KIND, true><<<(unsigned)grid, kThreads, 0, s>>>(a);
+        else wxpy_reduce_kernel<KIND, false><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    } else {
+        // staged shapes (ring stages, resident blocks): 1 (4, 2), 2 (3, 3), 3 (2, 3)
+        cudaError_t le = variant == 1   ? launch_staged<KIND, 4, 2>(a, dp, s)
+                         : variant == 2 ? launch_staged<KIND, 3, 3>(a, dp, s)
+                                        : launch_staged<KIND, 2, 3>(a, dp, s);
+        if (le != cudaSuccess) return fail_cuda(le, "staged reduce launch");
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? WXPY_OK : fail_cuda(e, "reduce launch");
 }
@@ -332,6 +688,34 @@ int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *
              void *stream) {
     return launch_reduce<1>(n, alpha, x, y, w, z, result, workspace, workspace_bytes,
                             (cudaStream_t)stream);
+}
+
+int wxpy_reduce_status(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned int fault = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&fault, g_reduce_fault, sizeof(fault));
+    const unsigned int zero = 0;
+    if (e == cudaSuccess && fault) e = cudaMemcpyToSymbol(g_reduce_fault, &zero, sizeof(zero));
+    if (e != cudaSuccess) return fail_cuda(e, "reduce status");
+    if (fault)
+        return fail(WXPY_ETIMEOUT, "a staged reduction's bounded wait ran out (mask %u: 1 producer, "
+                    "2 consumer, 4 exchange)", fault);
+    return WXPY_OK;
+}
+
+int wxpy_debug_reduce_drop_chunk(int64_t chunk) {
+    if (chunk < -1) return fail(WXPY_EINVAL, "chunk must be >= -1");
+    g_reduce_drop.store(chunk);
+    return WXPY_OK;
+}
+
+int wxpy_reduce_variant(int variant) {
+    if (variant < -1 || variant >= kReduceVariants)
+        return fail(WXPY_EINVAL, "variant must be -1..%d", kReduceVariants - 1);
+    g_reduce_variant.store(variant);
+    return WXPY_OK;
 }
 
 int wxpy_reduce_pipes(int mul_sixteenths) {

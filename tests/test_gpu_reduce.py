@@ -1,7 +1,7 @@
 """GPU parity of the update fused with a reduction (wxpy_norm2, wxpy_dot)
 through the C ABI: w and the result bit for bit against the oracle of
 reduce_oracle.c (NaN by class) -- sizes around every tile boundary and
-several tiles per block, the 32-byte and element paths, exact aliasing,
+several tiles per block, the staged and element paths, exact aliasing,
 every product split, special values, the tree's worked examples, CUDA-graph
 replay, and the full n = 2^26 case compared in full."""
 import math
@@ -26,6 +26,7 @@ SIZES = (0, 1, 5, T - 1, T, T + 1, 3 * T + 77, 100003, 1_000_003)
 def _pipes():
     yield
     wx.wxpy_reduce_pipes(-1)
+    wx.wxpy_reduce_variant(-1)
 
 
 def same_scalar(got, want):
@@ -57,9 +58,11 @@ def want(kind, alpha, xh, yh, zh):
 
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
+@pytest.mark.parametrize("variant", [-1, 1, 3])
 @pytest.mark.parametrize("mul", [-1, 0, 5, 16])
 @pytest.mark.parametrize("offs", [(0, 0, 0, 0), (8, 8, 8, 8), (0, 16, 8, 24)])
-def test_parity(kind, mul, offs):
+def test_parity(kind, variant, mul, offs):
+    wx.wxpy_reduce_variant(variant)
     wx.wxpy_reduce_pipes(mul)
     for n in SIZES:
         alpha, xh, yh = synth.vectors(synth.BASE_SEED + 500 + n, n)
@@ -68,6 +71,49 @@ def test_parity(kind, mul, offs):
         w_want, r_want = want(kind, alpha, xh, yh, zh)
         assert same_vec(w_got, w_want), (kind, n, offs)
         assert same_scalar(r_got, r_want), (kind, n, offs, r_got, r_want)
+
+
+@pytest.mark.parametrize("kind", ["norm2", "dot"])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3])
+@pytest.mark.parametrize("mul", [-1, 0, 7])
+@pytest.mark.parametrize("offs", [(0, 0, 0, 0), (32, 64, 96, 160), (16, 16, 16, 16)])
+def test_many_tiles_per_block(kind, variant, mul, offs):
+    """2^24 + 12345 elements: several tiles per block of every kernel variant
+    (every exchange slot and ring stage of the staged ones reused), a ragged
+    last tile; the 16-byte offsets take the element path."""
+    wx.wxpy_reduce_variant(variant)
+    wx.wxpy_reduce_pipes(mul)
+    n = (1 << 24) + 12345
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + 520, n)
+    zh = synth.uniform_pm1(synth.BASE_SEED + 521, synth.TAG_Y, n)
+    w_got, r_got = run(kind, alpha, xh, yh, zh, offs)
+    w_want, r_want = want(kind, alpha, xh, yh, zh)
+    assert same_vec(w_got, w_want), (kind, offs)
+    assert same_scalar(r_got, r_want), (kind, offs, r_got, r_want)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The producer owning chunk 11 stops before copying it: that block's
+    consumers give up after their one-second bound, the host reads
+    WXPY_ETIMEOUT, and the next launch on the same context is exact."""
+    n = 1 << 20
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + 530, n)
+    x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+    wx.wxpy_reduce_variant(1)
+    wx.wxpy_reduce_status()  # clean start
+    try:
+        wx.wxpy_debug_reduce_drop_chunk(11)
+        wx.wxpy_norm2(alpha, x, y)
+        with pytest.raises(wx.WxpyError) as e:
+            wx.wxpy_reduce_status()
+        assert e.value.status == wx.WXPY_ETIMEOUT
+    finally:
+        wx.wxpy_debug_reduce_drop_chunk(-1)
+    wx.wxpy_reduce_status()  # the record was cleared
+    w, res = wx.wxpy_norm2(alpha, x, y)
+    wx.wxpy_reduce_status()
+    w_want, r_want = oracle.wxpy_norm2(alpha, xh, yh)
+    assert same_vec(w.cpu().numpy(), w_want) and same_scalar(res.item(), r_want)
 
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
