@@ -716,10 +716,10 @@ def measure_vecops(wx, torch, dev, stream, peak, reps=10):
 def measure_reduce(wx, torch, dev, stream, peak, reps=10):
     """The update fused with a reduction of its result, n = 2^26: GB/s of
     algorithmic bytes (norm2: x, y read and w written, 24 B/element; dot: z
-    read too, 32 B) under each product split (sixteenths of the tiles whose
-    products run in the integer pipelines), and plain wxpy() on the same
-    vectors for the cost
-    of the fused reduction."""
+    read too, 32 B) after the configuration search (wxpy_reduce_tune, n =
+    2^24), under each product split of the searched kernel (sixteenths of the
+    tiles whose products run in the integer pipelines), and plain wxpy() on
+    the same vectors for the cost of the fused reduction."""
     n = 1 << 26
     x, y, z = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
     for k, t in enumerate((x, y, z)):
@@ -743,6 +743,10 @@ def measure_reduce(wx, torch, dev, stream, peak, reps=10):
     norm2 = lambda: wx.wxpy_norm2(-0.625, x, y, w=w, result=res, workspace=ws)
     dot = lambda: wx.wxpy_dot(-0.625, x, y, z, w=w, result=res, workspace=ws)
     gbs = lambda nbytes, ms: nbytes / (ms / 1e3) / 1e9
+    # the configuration search first: the timed calls below use its winners
+    t0 = time.time()
+    search = wx.wxpy_reduce_tune(1 << 24)
+    search_s = time.time() - t0
     splits = []
     for mul in (0, 4, 8, 12, 16):
         wx.wxpy_reduce_pipes(mul)
@@ -755,7 +759,8 @@ def measure_reduce(wx, torch, dev, stream, peak, reps=10):
            "norm2": {"gbs": gbs(24 * n, ms_n), "frac_of_peak": gbs(24 * n, ms_n) / peak, "ms": ms_n},
            "dot": {"gbs": gbs(32 * n, ms_d), "frac_of_peak": gbs(32 * n, ms_d) / peak, "ms": ms_d},
            "wxpy_alone": {"gbs": gbs(24 * n, ms_w), "ms": ms_w},
-           "norm2_time_vs_wxpy": ms_n / ms_w, "splits": splits}
+           "norm2_time_vs_wxpy": ms_n / ms_w, "splits": splits,
+           "search": {"n": 1 << 24, "seconds": search_s, "kinds": search}}
     del x, y, z, w, ws
     torch.cuda.empty_cache()
     return out

@@ -331,8 +331,17 @@ int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *
 /* The share, in sixteenths, of the tiles whose two products per element
  * (alpha*x and the term) run as the exactly rounded integer-pipeline product
  * instead of FP64 instructions (a rotation over blocks and tiles): 0..16, -1
- * the default.  Same bits either way.  Process-wide. */
+ * the searched value (wxpy_reduce_tune) or else the default.  Same bits
+ * either way.  Process-wide; the same -1 rule holds for wxpy_reduce_variant
+ * and wxpy_reduce_sum_levels. */
 int wxpy_reduce_pipes(int mul_sixteenths);
+
+/* wxpy_norm2 on the register-loaded kernel: how many of the three tree
+ * levels summed inside a thread (the first three of each tile) run as the
+ * exactly rounded integer-pipeline sum of two non-negative values instead of
+ * FP64 instructions: 0..3, -1 the default.  Same bits either way.
+ * Process-wide. */
+int wxpy_reduce_sum_levels(int levels);
 
 /* The kernel of wxpy_norm2 / wxpy_dot for 32-byte co-aligned pointers
  * (other alignments always take the element path): 0 register-loaded (a
@@ -341,6 +350,39 @@ int wxpy_reduce_pipes(int mul_sixteenths);
  * resident blocks per SM) = (4, 2), (3, 3), (2, 3); -1 the default.  Same
  * bits for every variant.  Process-wide. */
 int wxpy_reduce_variant(int variant);
+
+typedef struct wxpy_reduce_tune_result {
+    int32_t kind;            /* 0 wxpy_norm2, 1 wxpy_dot */
+    int32_t variant;         /* the winning configuration (see wxpy_reduce_variant) */
+    int32_t mul_sixteenths;
+    int32_t sum_levels;      /* norm2 only; 0 for dot */
+    int32_t candidates;      /* configurations timed */
+    int32_t rejected;        /* configurations whose w or result differed from the reference */
+    double best_us;          /* median device time of the winner, L2 flushed */
+    double default_us;       /* the built-in default configuration, same conditions */
+    double gbs;              /* algorithmic bytes (24 or 32 per element) / best_us */
+} wxpy_reduce_tune_result;
+
+/* The empirical search of Sec. 2 for the fused reductions.  For each of
+ * wxpy_norm2 and wxpy_dot, on generator inputs of n elements per vector: the
+ * register-loaded kernel with every operation in FP64 gives the reference w
+ * and result; every candidate configuration (the register-loaded kernel at
+ * product shares 0, 4, .., 16 sixteenths; for norm2, 1..3 integer tree
+ * levels at the best share and at half of it; the three staged shapes at the
+ * best share) is run once and compared with it bit for bit -- a single
+ * differing bit of w or of the result rejects it -- and timed as the median
+ * of five runs, each after an L2 flush.  The fastest verified configuration
+ * becomes the operation's configuration for later calls whose knobs are left
+ * at -1, and is saved and loaded with the tune cache.  `results` (2 entries)
+ * may be NULL.  Allocates about 5 n doubles of scratch while it runs, on the
+ * current device.  Errors: WXPY_EINVAL (n <= 0), WXPY_ENOMEM, WXPY_ECUDA,
+ * WXPY_EMISMATCH (every configuration rejected). */
+int wxpy_reduce_tune(int64_t n, wxpy_reduce_tune_result *results);
+
+/* The searched configuration of a reduction (kind 0 norm2, 1 dot; all -1
+ * when not searched); set installs one or clears it (all -1). */
+int wxpy_reduce_tuned_get(int kind, int *variant, int *mul_sixteenths, int *sum_levels);
+int wxpy_reduce_tuned_set(int kind, int variant, int mul_sixteenths, int sum_levels);
 
 /* Synchronises the current device, then returns WXPY_ETIMEOUT (and clears
  * the record) if a bounded wait of a staged reduction launched since the last

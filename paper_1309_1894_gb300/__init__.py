@@ -13,8 +13,8 @@ from .binding import (  # noqa: F401
     wxpy_axpy, wxpy_aypx, wxpy_axpby, wxpy_axpbypcz, wxpy_maxpy, wxpy_pointwise_mult,
     wxpy_vecops_pipes, wxpy_vecops_status, wxpy_vecops_tune, wxpy_vecops_tuned_get,
     wxpy_vecops_tuned_set, wxpy_debug_vecops_drop_tile,
-    wxpy_norm2, wxpy_dot, wxpy_reduce_pipes, wxpy_reduce_status, wxpy_reduce_variant,
-    wxpy_debug_reduce_drop_chunk,
+    wxpy_norm2, wxpy_dot, wxpy_reduce_pipes, wxpy_reduce_status, wxpy_reduce_variant, wxpy_reduce_sum_levels,
+    wxpy_debug_reduce_drop_chunk, wxpy_reduce_tune, wxpy_reduce_tuned_get, wxpy_reduce_tuned_set,
     reduce_workspace,
     VEC_AXPBYPCZ, VEC_PMULT, VEC_AXPBY, VEC_CLASSES, VEC_CLASS_NAMES,
     wxpy_reference, wxpy_lookup, wxpy_classify,

@@ -90,6 +90,19 @@ class VecopsTuneResult(ctypes.Structure):
         return d
 
 
+class ReduceTuneResult(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("mul_sixteenths", ctypes.c_int32), ("sum_levels", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("best_us", ctypes.c_double), ("default_us", ctypes.c_double),
+                ("gbs", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["op"] = ("norm2", "dot")[self.kind]
+        return d
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -144,6 +157,11 @@ SIGNATURES = {
     "wxpy_reduce_pipes": (_INT, [_INT]),
     "wxpy_reduce_status": (_INT, []),
     "wxpy_reduce_variant": (_INT, [_INT]),
+    "wxpy_reduce_sum_levels": (_INT, [_INT]),
+    "wxpy_reduce_tune": (_INT, [_I64, ctypes.c_void_p]),
+    "wxpy_reduce_tuned_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT),
+                                     ctypes.POINTER(_INT)]),
+    "wxpy_reduce_tuned_set": (_INT, [_INT, _INT, _INT, _INT]),
     "wxpy_debug_reduce_drop_chunk": (_INT, [_I64]),
     "wxpy_vecops_tune": (_INT, [_I64, ctypes.POINTER(VecopsTuneResult)]),
     "wxpy_vecops_tuned_get": (_INT, [_INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
@@ -420,6 +438,30 @@ def wxpy_reduce_variant(variant: int = -1) -> None:
     """Kernel of the fused reductions for co-aligned pointers: 0 register-
     loaded, 1..3 staged shapes, -1 the default (same bits for all)."""
     check(lib().wxpy_reduce_variant(variant), "wxpy_reduce_variant")
+
+
+def wxpy_reduce_sum_levels(levels: int = -1) -> None:
+    """norm2: in-thread tree levels summed in the integer pipelines (0..3, -1 default)."""
+    check(lib().wxpy_reduce_sum_levels(levels), "wxpy_reduce_sum_levels")
+
+
+def wxpy_reduce_tune(n: int) -> list[dict]:
+    """The configuration search of wxpy_norm2 and wxpy_dot on n-element vectors."""
+    res = (ReduceTuneResult * 2)()
+    check(lib().wxpy_reduce_tune(n, res), "wxpy_reduce_tune")
+    return [r.as_dict() for r in res]
+
+
+def wxpy_reduce_tuned_get(kind: int) -> tuple[int, int, int]:
+    v, m, l = _INT(), _INT(), _INT()
+    check(lib().wxpy_reduce_tuned_get(kind, ctypes.byref(v), ctypes.byref(m), ctypes.byref(l)),
+          "wxpy_reduce_tuned_get")
+    return v.value, m.value, l.value
+
+
+def wxpy_reduce_tuned_set(kind: int, variant: int, mul_sixteenths: int, sum_levels: int) -> None:
+    check(lib().wxpy_reduce_tuned_set(kind, variant, mul_sixteenths, sum_levels),
+          "wxpy_reduce_tuned_set")
 
 
 def wxpy_reduce_status() -> None:

@@ -135,6 +135,21 @@ VecPipes vecops_default(int cls);
 bool vecops_tuned_load(int cls, VecPipes *p);
 void vecops_tuned_store(int cls, const VecPipes *p);  // nullptr clears
 
+// reduce.cu: the fused reductions (kind 0 norm2, 1 dot) under an explicit
+// configuration, and the table of searched configurations.
+struct ReduceConfig {
+    int variant;  // 0 register-loaded, 1..3 staged shapes
+    int mul;      // product sixteenths 0..16
+    int suml;     // norm2: in-thread tree levels summed in the integer pipelines, 0..3
+};
+ReduceConfig reduce_default(int kind);
+bool reduce_config_valid(int kind, ReduceConfig c);
+int reduce_run(int kind, int64_t n, double alpha, const double *x, const double *y, double *w,
+               const double *z, double *result, void *workspace, int64_t ws_bytes, ReduceConfig c,
+               cudaStream_t s);
+bool reduce_tuned_load(int kind, ReduceConfig *c);
+void reduce_tuned_store(int kind, const ReduceConfig *c);  // nullptr clears
+
 cudaError_t launch_reference(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s);
 SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy);
 

@@ -56,6 +56,7 @@
 #include <cstring>
 
 #include "bulk.cuh"
+#include "fp64_addpos.cuh"
 #include "fp64_emu.cuh"
 #include "fp64_mul.cuh"
 #include "internal.h"
@@ -82,6 +83,25 @@ struct ReduceArgs {
 
 __device__ __forceinline__ uint64_t bits_of(double v) { return (uint64_t)__double_as_longlong(v); }
 __device__ __forceinline__ double double_of(uint64_t b) { return __longlong_as_double((long long)b); }
+
+static __device__ __noinline__ uint64_t add_rn_hw_bits(uint64_t ua, uint64_t ub) {
+    return bits_of(__dadd_rn(double_of(ua), double_of(ub)));
+}
+
+// RN(a + b) of two sums of squares (non-negative): the integer-pipeline sum
+// when INT, else the FP64 instruction.
+template <bool INT>
+__device__ __forceinline__ double tree_add(double a, double b) {
+    if constexpr (INT) {
+        const uint64_t ua = opaque_bits(a), ub = opaque_bits(b);
+        bool slow = false;
+        uint64_t r = add_pos_core(ua, ub, slow);
+        if (slow) r = add_rn_hw_bits(ua, ub);  // out of line
+        return double_of(r);
+    } else {
+        return __dadd_rn(a, b);
+    }
+}
 
 // w and the term of one element.  EMU: both products in the integer pipelines.
 template <int KIND, bool EMU>
@@ -145,8 +165,11 @@ __device__ __forceinline__ void vector_terms(const ReduceArgs &a, int64_t base, 
 }
 
 // The sum of tile `tile`; valid in thread 0.  red: 256 x 4 doubles of shared memory.
-template <int KIND, bool VEC, bool EMU>
+// SUML (norm2 only): the first SUML of the three in-thread tree levels run as
+// integer-pipeline sums of non-negative values.
+template <int KIND, bool VEC, bool EMU, int SUML = 0>
 __device__ double tile_sum(const ReduceArgs &a, int64_t tile, double (*red)[4]) {
+    static_assert(SUML == 0 || KIND == 0, "integer tree sums need non-negative terms");
     const int t = threadIdx.x, lane = t & 31;
     const int64_t t0 = tile * kTile + 4 * t;
     // bits 12..10: r[j] = tree over k = j, j+4 (bit 12), then j, j+2 (bit 11), then bit 10
@@ -157,14 +180,14 @@ __device__ double tile_sum(const ReduceArgs &a, int64_t tile, double (*red)[4]) 
         vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * j, lo);
         vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * (j + 4), hi);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r[j][q] = __dadd_rn(lo[q], hi[q]);
+        for (int q = 0; q < 4; ++q) r[j][q] = tree_add<(SUML >= 1)>(lo[q], hi[q]);
     }
     double v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        r[0][q] = __dadd_rn(r[0][q], r[2][q]);
-        r[1][q] = __dadd_rn(r[1][q], r[3][q]);
-        v[q] = __dadd_rn(r[0][q], r[1][q]);
+        r[0][q] = tree_add<(SUML >= 2)>(r[0][q], r[2][q]);
+        r[1][q] = tree_add<(SUML >= 2)>(r[1][q], r[3][q]);
+        v[q] = tree_add<(SUML >= 3)>(r[0][q], r[1][q]);
     }
     // bits 9..7: threads t and t + 128, t + 64, t + 32 through shared memory
 #pragma unroll
@@ -229,7 +252,7 @@ __device__ __forceinline__ void finish_grid(const ReduceArgs &a, bool &last) {
 // Register-loaded path: four resident blocks (64 registers), measured 4-5 %
 // faster than three.  VEC: full tiles by 32-byte vectors (co-aligned
 // pointers); the last tile, and every tile otherwise, element by element.
-template <int KIND, bool VEC>
+template <int KIND, bool VEC, int SUML = 0>
 __global__ void __launch_bounds__(kThreads, 4) wxpy_reduce_kernel(const ReduceArgs a) {
     __shared__ double red[kThreads][4];
     __shared__ bool last;
@@ -238,8 +261,8 @@ __global__ void __launch_bounds__(kThreads, 4) wxpy_reduce_kernel(const ReduceAr
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         double s;
         if (tile >= full) s = tile_sum<KIND, false, false>(a, tile, red);
-        else if ((int)slot < a.mul_sixteenths) s = tile_sum<KIND, VEC, true>(a, tile, red);
-        else s = tile_sum<KIND, VEC, false>(a, tile, red);
+        else if ((int)slot < a.mul_sixteenths) s = tile_sum<KIND, VEC, true, SUML>(a, tile, red);
+        else s = tile_sum<KIND, VEC, false, SUML>(a, tile, red);
         if (threadIdx.x == 0) a.partial[tile] = s;
         slot = (slot + 1u) & 15u;
     }
@@ -570,6 +593,9 @@ int blocks_per_sm(int device) {
 std::atomic<int> g_reduce_mul{-1};
 std::atomic<long long> g_reduce_drop{-1};
 std::atomic<int> g_reduce_variant{-1};
+std::atomic<int> g_reduce_sum_levels{-1};
+std::atomic<int> g_reduce_tuned[2] = {-1, -1};  // (variant << 10) | (suml << 5) | mul
+constexpr int kDefaultSumLevels = 0;
 constexpr int kReduceVariants = 4;
 // Measured on GB300 at n = 2^26 with every product in the integer pipelines
 // (GB/s of algorithmic bytes, norm2 / dot): register-loaded 4482 / 5485;
@@ -589,10 +615,22 @@ bool overlaps(const void *a, int64_t abytes, const void *b, int64_t bbytes) {
     return pa < pb + (uintptr_t)bbytes && pb < pa + (uintptr_t)abytes;
 }
 
+// The configuration of a call: each knob set explicitly (>= 0) wins, then the
+// searched configuration of the operation, then the built-in default.
+ReduceConfig config_for(int kind) {
+    ReduceConfig c = reduce_default(kind);
+    reduce_tuned_load(kind, &c);
+    const int v = g_reduce_variant.load(), m = g_reduce_mul.load(), l = g_reduce_sum_levels.load();
+    if (v >= 0) c.variant = v;
+    if (m >= 0) c.mul = m;
+    if (l >= 0) c.suml = l;
+    return c;
+}
+
 template <int KIND>
 int launch_reduce(int64_t n, double alpha, const double *x, const double *y, double *w,
                   const double *z, double *result, void *workspace, int64_t ws_bytes,
-                  cudaStream_t s) {
+                  ReduceConfig cfg, cudaStream_t s) {
     if (n < 0) return fail(WXPY_EINVAL, "n = %lld is negative", (long long)n);
     if (n > ((int64_t)1 << 40)) return fail(WXPY_EINVAL, "n too large");
     if (!result || ((uintptr_t)result & 7)) return fail(WXPY_EINVAL, "null or misaligned result");
@@ -640,20 +678,27 @@ int launch_reduce(int64_t n, double alpha, const double *x, const double *y, dou
     uint64_t ab;
     std::memcpy(&ab, &alpha, 8);
     a.ca = mul_coef_of(ab);
-    const int m = g_reduce_mul.load();
-    a.mul_sixteenths = m < 0 ? kDefaultMulSixteenths : m;
+    a.mul_sixteenths = cfg.mul;
     a.drop_chunk = g_reduce_drop.load();
     uintptr_t any = (uintptr_t)x | (uintptr_t)y | (uintptr_t)w | (KIND == 1 ? (uintptr_t)z : 0);
     const bool vec = (any & 31u) == 0;
     e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return fail_cuda(e, "reduce ticket");
-    const int v = g_reduce_variant.load();
-    const int variant = !vec ? 0 : v < 0 ? kDefaultVariant[KIND] : v;
+    const int variant = vec ? cfg.variant : 0;
     if (variant == 0) {
         const int nb = vec ? blocks_per_sm<KIND, true>(dp->device) : blocks_per_sm<KIND, false>(dp->device);
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)dp->sm_count * nb, a.ntiles));
-        if (vec) wxpy_reduce_kernel<KIND, true><<<(unsigned)grid, kThreads, 0, s>>>(a);
-        else wxpy_reduce_kernel<KIND, false><<<(unsigned)grid, kThreads, 0, s>>>(a);
+        if (!vec) wxpy_reduce_kernel<KIND, false><<<(unsigned)grid, kThreads, 0, s>>>(a);
+        else if constexpr (KIND == 0) {
+            switch (cfg.suml) {
+                case 0: wxpy_reduce_kernel<0, true, 0><<<(unsigned)grid, kThreads, 0, s>>>(a); break;
+                case 1: wxpy_reduce_kernel<0, true, 1><<<(unsigned)grid, kThreads, 0, s>>>(a); break;
+                case 2: wxpy_reduce_kernel<0, true, 2><<<(unsigned)grid, kThreads, 0, s>>>(a); break;
+                default: wxpy_reduce_kernel<0, true, 3><<<(unsigned)grid, kThreads, 0, s>>>(a);
+            }
+        } else {
+            wxpy_reduce_kernel<KIND, true><<<(unsigned)grid, kThreads, 0, s>>>(a);
+        }
     } else {
         // staged shapes (ring stages, resident blocks): 1 (4, 2), 2 (3, 3), 3 (2, 3)
         cudaError_t le = variant == 1   ? launch_staged<KIND, 4, 2>(a, dp, s)
@@ -666,6 +711,40 @@ int launch_reduce(int64_t n, double alpha, const double *x, const double *y, dou
 }
 
 }  // namespace
+
+ReduceConfig reduce_default(int kind) {
+    return ReduceConfig{kDefaultVariant[kind == 1 ? 1 : 0], kDefaultMulSixteenths,
+                        kind == 0 ? kDefaultSumLevels : 0};
+}
+
+bool reduce_config_valid(int kind, ReduceConfig c) {
+    return c.variant >= 0 && c.variant < kReduceVariants && c.mul >= 0 && c.mul <= 16 &&
+           c.suml >= 0 && c.suml <= 3 && (kind == 0 || c.suml == 0);
+}
+
+bool reduce_tuned_load(int kind, ReduceConfig *c) {
+    if (kind < 0 || kind > 1) return false;
+    const int v = g_reduce_tuned[kind].load();
+    if (v < 0) return false;
+    c->variant = v >> 10;
+    c->suml = (v >> 5) & 31;
+    c->mul = v & 31;
+    return true;
+}
+
+void reduce_tuned_store(int kind, const ReduceConfig *c) {
+    if (kind < 0 || kind > 1) return;
+    g_reduce_tuned[kind].store(c ? (c->variant << 10) | (c->suml << 5) | c->mul : -1);
+}
+
+int reduce_run(int kind, int64_t n, double alpha, const double *x, const double *y, double *w,
+               const double *z, double *result, void *workspace, int64_t ws_bytes, ReduceConfig c,
+               cudaStream_t s) {
+    if (!reduce_config_valid(kind, c)) return fail(WXPY_EINVAL, "bad reduce configuration");
+    return kind == 1 ? launch_reduce<1>(n, alpha, x, y, w, z, result, workspace, ws_bytes, c, s)
+                     : launch_reduce<0>(n, alpha, x, y, w, nullptr, result, workspace, ws_bytes, c, s);
+}
+
 }  // namespace wx
 
 using namespace wx;
@@ -680,14 +759,14 @@ int64_t wxpy_reduce_workspace_bytes(int64_t n) {
 int wxpy_norm2(int64_t n, double alpha, const double *x, const double *y, double *w,
                double *result, void *workspace, int64_t workspace_bytes, void *stream) {
     return launch_reduce<0>(n, alpha, x, y, w, nullptr, result, workspace, workspace_bytes,
-                            (cudaStream_t)stream);
+                            config_for(0), (cudaStream_t)stream);
 }
 
 int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *w,
              const double *z, double *result, void *workspace, int64_t workspace_bytes,
              void *stream) {
     return launch_reduce<1>(n, alpha, x, y, w, z, result, workspace, workspace_bytes,
-                            (cudaStream_t)stream);
+                            config_for(1), (cudaStream_t)stream);
 }
 
 int wxpy_reduce_status(void) {
@@ -708,6 +787,12 @@ int wxpy_reduce_status(void) {
 int wxpy_debug_reduce_drop_chunk(int64_t chunk) {
     if (chunk < -1) return fail(WXPY_EINVAL, "chunk must be >= -1");
     g_reduce_drop.store(chunk);
+    return WXPY_OK;
+}
+
+int wxpy_reduce_sum_levels(int levels) {
+    if (levels < -1 || levels > 3) return fail(WXPY_EINVAL, "levels must be -1..3");
+    g_reduce_sum_levels.store(levels);
     return WXPY_OK;
 }
 

@@ -371,6 +371,22 @@ int cache_save(const char *path) {
         }
         out += "\n  ],";
     }
+    {
+        out += "\n  \"reduce\": [";
+        bool rfirst = true;
+        for (int k = 0; k < 2; ++k) {
+            ReduceConfig rc;
+            if (!reduce_tuned_load(k, &rc)) continue;
+            char buf[140];
+            std::snprintf(buf, sizeof buf,
+                          "%s\n    {\"kind\": %d, \"variant\": %d, \"mul_sixteenths\": %d, "
+                          "\"sum_levels\": %d}",
+                          rfirst ? "" : ",", k, rc.variant, rc.mul, rc.suml);
+            out += buf;
+            rfirst = false;
+        }
+        out += "\n  ],";
+    }
     out += "\n  \"entries\": [";
     bool first = true;
     for (int k = 0; k < kTuneKeys; ++k) {
@@ -486,9 +502,29 @@ int cache_load(const char *path, const char *expect_device) {
             q = r;
         }
     }
+    // Optional searched configurations of the fused reductions.
+    std::vector<std::pair<int, ReduceConfig>> red;
+    size_t rpos = s.find("\"reduce\"");
+    if (rpos != std::string::npos) {
+        const size_t rend = s.find(']', rpos);
+        if (rend == std::string::npos) return fail(WXPY_EINVAL, "%s: unterminated reduce", path);
+        size_t q = rpos;
+        while ((q = s.find('{', q + 1)) != std::string::npos && q < rend) {
+            const size_t r = s.find('}', q);
+            long long k = -1, v = -1, m = -1, l = -1;
+            if (r == std::string::npos || !find_int(s, q, r, "kind", &k) ||
+                !find_int(s, q, r, "variant", &v) || !find_int(s, q, r, "mul_sixteenths", &m) ||
+                !find_int(s, q, r, "sum_levels", &l) || k < 0 || k > 1 ||
+                !reduce_config_valid((int)k, ReduceConfig{(int)v, (int)m, (int)l}))
+                return fail(WXPY_EINVAL, "%s: malformed reduce entry", path);
+            red.push_back({(int)k, ReduceConfig{(int)v, (int)m, (int)l}});
+            q = r;
+        }
+    }
     for (auto &kv : entries) g_tuned[kv.first].store(kv.second);
     if (have_batch) set_batch_shape(bs);
     for (auto &cv : vec) vecops_tuned_store(cv.first, &cv.second);
+    for (auto &rc : red) reduce_tuned_store(rc.first, &rc.second);
     return WXPY_OK;
 }
 
@@ -544,6 +580,7 @@ int wxpy_tune_set(int tune_key, int variant_id) {
 int wxpy_tune_clear(void) {
     for (auto &t : g_tuned) t.store(-1);
     for (int c = 0; c < WXPY_VEC_CLASSES; ++c) vecops_tuned_store(c, nullptr);
+    for (int k = 0; k < 2; ++k) reduce_tuned_store(k, nullptr);
     return WXPY_OK;
 }
 

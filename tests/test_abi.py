@@ -180,6 +180,9 @@ def test_vecops_validation_before_cuda(lib):
     for bad in (-2, 4):
         assert lib.wxpy_reduce_variant(bad) == wx.WXPY_EINVAL
     assert lib.wxpy_reduce_variant(-1) == 0
+    for bad in (-2, 4):
+        assert lib.wxpy_reduce_sum_levels(bad) == wx.WXPY_EINVAL
+    assert lib.wxpy_reduce_sum_levels(-1) == 0
 
 
 def test_reduce_validation_before_cuda(lib):

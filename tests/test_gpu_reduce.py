@@ -27,6 +27,7 @@ def _pipes():
     yield
     wx.wxpy_reduce_pipes(-1)
     wx.wxpy_reduce_variant(-1)
+    wx.wxpy_reduce_sum_levels(-1)
 
 
 def same_scalar(got, want):
@@ -92,6 +93,21 @@ def test_many_tiles_per_block(kind, variant, mul, offs):
     assert same_scalar(r_got, r_want), (kind, offs, r_got, r_want)
 
 
+@pytest.mark.parametrize("suml", [1, 2, 3])
+@pytest.mark.parametrize("mul", [0, 16])
+def test_integer_tree_sums(suml, mul):
+    """norm2 with the first 1..3 in-thread tree levels summed in the integer
+    pipelines: every size of the parity set, several tiles per block."""
+    wx.wxpy_reduce_sum_levels(suml)
+    wx.wxpy_reduce_pipes(mul)
+    for n in SIZES + ((1 << 24) + 12345,):
+        alpha, xh, yh = synth.vectors(synth.BASE_SEED + 540 + n, n)
+        w_got, r_got = run("norm2", alpha, xh, yh, None, (0, 0, 0, 0))
+        w_want, r_want = oracle.wxpy_norm2(alpha, xh, yh)
+        assert same_vec(w_got, w_want), n
+        assert same_scalar(r_got, r_want), (n, r_got, r_want)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """The producer owning chunk 11 stops before copying it: that block's
     consumers give up after their one-second bound, the host reads
@@ -118,8 +134,10 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
 @pytest.mark.parametrize("mul", [0, 16])
-def test_special_and_wide_values(kind, mul):
+@pytest.mark.parametrize("suml", [0, 3])
+def test_special_and_wide_values(kind, mul, suml):
     wx.wxpy_reduce_pipes(mul)
+    wx.wxpy_reduce_sum_levels(suml)
     sv = np.array(pins.special_values())
     rng = np.random.default_rng(3)
     for n in (len(sv) ** 2, 3 * T + 5):
@@ -247,3 +265,40 @@ def test_small_workspace_is_refused():
     with pytest.raises(wx.WxpyError) as e:
         wx.wxpy_norm2(1.0, x, x, workspace=ws)
     assert e.value.status == wx.WXPY_EINVAL
+
+
+def test_configuration_search(tmp_path):
+    """wxpy_reduce_tune: every candidate verified (none rejected), the winner
+    installed and used by later calls (still the oracle's bits), and saved and
+    loaded with the tune cache."""
+    try:
+        res = wx.wxpy_reduce_tune(1 << 21)
+        assert [r["op"] for r in res] == ["norm2", "dot"]
+        for r in res:
+            assert r["rejected"] == 0, r
+            # norm2: 5 product shares, 3 tree levels at the best share and at half of it
+            # (one fewer set when half equals the best), 3 staged shapes; dot: 5 + 3
+            if r["kind"] == 0:
+                assert r["candidates"] in (5 + 3 + 3, 5 + 6 + 3), r
+            else:
+                assert r["candidates"] == 8 and r["sum_levels"] == 0, r
+            assert 0 < r["best_us"] <= r["default_us"] * 1.5, r
+            assert wx.wxpy_reduce_tuned_get(r["kind"]) == (r["variant"], r["mul_sixteenths"],
+                                                           r["sum_levels"])
+        n = 3 * T + 901
+        alpha, xh, yh = synth.vectors(synth.BASE_SEED + 560, n)
+        zh = synth.uniform_pm1(synth.BASE_SEED + 561, synth.TAG_Y, n)
+        for kind in ("norm2", "dot"):
+            w_got, r_got = run(kind, alpha, xh, yh, zh, (0, 0, 0, 0))
+            w_want, r_want = want(kind, alpha, xh, yh, zh)
+            assert same_vec(w_got, w_want) and same_scalar(r_got, r_want), kind
+        path = str(tmp_path / "tune.json")
+        wx.wxpy_tune_cache_save(path)
+        wx.wxpy_tune_clear()
+        assert wx.wxpy_reduce_tuned_get(0) == (-1, -1, -1)
+        wx.wxpy_tune_cache_load(path, check_device=True)
+        for r in res:
+            assert wx.wxpy_reduce_tuned_get(r["kind"]) == (r["variant"], r["mul_sixteenths"],
+                                                           r["sum_levels"])
+    finally:
+        wx.wxpy_tune_clear()

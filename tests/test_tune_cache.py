@@ -106,3 +106,52 @@ def test_malformed_vecops_entry_stores_nothing(tmp_path, entry):
     assert e.value.status == wx.WXPY_EINVAL
     assert wx.wxpy_vecops_tuned_get(2) == (-1, -1)
     assert wx.wxpy_tune_get(1) == -1
+
+
+def test_reduce_config_set_get_clear():
+    assert wx.wxpy_reduce_tuned_get(0) == (-1, -1, -1)
+    wx.wxpy_reduce_tuned_set(0, 2, 12, 1)
+    assert wx.wxpy_reduce_tuned_get(0) == (2, 12, 1)
+    wx.wxpy_reduce_tuned_set(0, -1, -1, -1)
+    assert wx.wxpy_reduce_tuned_get(0) == (-1, -1, -1)
+    wx.wxpy_reduce_tuned_set(1, 0, 16, 0)
+    wx.wxpy_tune_clear()  # drops the searched configurations too
+    assert wx.wxpy_reduce_tuned_get(1) == (-1, -1, -1)
+    for bad in ((2, 0, 16, 0), (-1, 0, 16, 0), (0, 4, 16, 0), (0, 0, 17, 0), (0, 0, 16, 4),
+                (1, 0, 16, 1)):  # dot's terms can be negative: no integer tree sums
+        with pytest.raises(wx.WxpyError) as e:
+            wx.wxpy_reduce_tuned_set(*bad)
+        assert e.value.status == wx.WXPY_EINVAL
+
+
+def test_load_reduce_section(tmp_path):
+    path = tmp_path / "r.json"
+    path.write_text(json.dumps({"format": "wxpy-tune-1", "device": "X",
+                                "vecops": [{"class": 3, "add_offload": 1, "mul_sixteenths": 10}],
+                                "reduce": [{"kind": 0, "variant": 0, "mul_sixteenths": 8,
+                                            "sum_levels": 2},
+                                           {"kind": 1, "variant": 3, "mul_sixteenths": 16,
+                                            "sum_levels": 0}],
+                                "entries": [{"key": 4, "variant": 11}]}))
+    wx.wxpy_tune_cache_load(str(path), check_device=False)
+    assert wx.wxpy_reduce_tuned_get(0) == (0, 8, 2)
+    assert wx.wxpy_reduce_tuned_get(1) == (3, 16, 0)
+    assert wx.wxpy_vecops_tuned_get(3) == (1, 10)
+    assert wx.wxpy_tune_get(4) == 11
+
+
+@pytest.mark.parametrize("entry", [{"kind": 2, "variant": 0, "mul_sixteenths": 2, "sum_levels": 0},
+                                   {"kind": 1, "variant": 0, "mul_sixteenths": 2, "sum_levels": 1},
+                                   {"kind": 0, "variant": 4, "mul_sixteenths": 2, "sum_levels": 0},
+                                   {"kind": 0, "variant": 0, "mul_sixteenths": 2}])
+def test_malformed_reduce_entry_stores_nothing(tmp_path, entry):
+    path = tmp_path / "bad.json"
+    path.write_text(json.dumps({"format": "wxpy-tune-1", "device": "X",
+                                "reduce": [{"kind": 0, "variant": 0, "mul_sixteenths": 6,
+                                            "sum_levels": 0}, entry],
+                                "entries": [{"key": 1, "variant": 2}]}))
+    with pytest.raises(wx.WxpyError) as e:
+        wx.wxpy_tune_cache_load(str(path), check_device=False)
+    assert e.value.status == wx.WXPY_EINVAL
+    assert wx.wxpy_reduce_tuned_get(0) == (-1, -1, -1)
+    assert wx.wxpy_tune_get(1) == -1
