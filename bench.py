@@ -889,7 +889,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="profiling mode: force this variant id instead of the tuned one")
     ap.add_argument("--vecop", default="",
-                    help="profiling mode: only run this kernel (axpbypcz, maxpy4, maxpy8, "
+                    help="profiling mode: only run this kernel (axpbypcz, axpby, maxpy4, maxpy8, "
                          "pointwise_mult, norm2, dot; serve: one 64-request server batch with "
                          "n up to SINGLE) on n = SINGLE, --reps times")
     ap.add_argument("--pipes", default="-1,-1",
@@ -939,8 +939,8 @@ def run_vecop(args):
     import paper_1309_1894_gb300 as wx
     from paper_1309_1894_gb300 import synth
     n = args.single
-    nvec = {"axpbypcz": 3, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3, "norm2": 3,
-            "dot": 4, "serve": 1}[args.vecop]
+    nvec = {"axpbypcz": 3, "axpby": 2, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3,
+            "norm2": 3, "dot": 4, "serve": 1}[args.vecop]
     v = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(nvec)]
     for k, t in enumerate(v):
         wx.wxpy_fill_uniform(t, synth.BASE_SEED + k, synth.TAG_X)
@@ -972,6 +972,8 @@ def run_vecop(args):
             wx.wxpy_dot(0.5, v[0], v[1], v[3], w=v[2], result=res, workspace=ws)
         elif args.vecop == "axpbypcz":
             wx.wxpy_axpbypcz(0.5, -0.25, 0.5, v[0], v[1], v[2])
+        elif args.vecop == "axpby":
+            wx.wxpy_axpby(0.5, -0.25, v[0], v[1])
         elif args.vecop == "pointwise_mult":
             wx.wxpy_pointwise_mult(v[0], v[1], v[2])
         else:
