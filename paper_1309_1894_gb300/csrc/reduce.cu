@@ -9,8 +9,18 @@
 // (e[i] = RN(e[i] + e[i + s]) for s = T/2, ..., 1, +0 past n); the tile sums,
 // padded with +0 to a power of two, are summed by the same tree.
 //
-// Staged path (x, y, w and z 32-byte co-aligned).  A persistent grid; each
-// block owns tiles blockIdx.x, blockIdx.x + gridDim.x, ...  One producer warp
+// Register-loaded kernel (the default).  A persistent grid of 256-thread
+// blocks, four per SM; a block takes a tile, thread t the 32-byte vectors at
+// 1024k + 4t (k = 0..7), so element i = 1024k + 4t + q has bits 12..10 = k,
+// 9..7 = warp, 6..2 = lane, 1..0 = q.  The halving tree reduces bits from the
+// top down, each level where its operands live: bits 12..10 inside the
+// thread, 9..7 across warps through shared memory, 6..2 by warp shuffles,
+// 1..0 inside lane 0.  With pointers that are not 32-byte co-aligned (and for
+// the last, ragged tile) the same threads read and write every element on its
+// own.  For norm2, the first 0..3 in-thread levels may run as the integer-
+// pipeline sum of non-negative values (fp64_addpos.cuh).
+//
+// Staged kernels (variants 1..3, co-aligned pointers).  One producer warp
 // copies a tile as eight 1024-element chunks of every input into a shared-
 // memory ring (bulk asynchronous copies completed on "full" mbarriers; a stage
 // is reused once all eight consumer warps have released it on its "empty"
@@ -18,26 +28,20 @@
 // consumer thread (warp v, lane l) takes the 16-byte pairs 128v + 64h + 2l
 // (h = 0, 1) of every chunk, so element i = 1024c + 128v + 64h + 2l + q has
 // bits 12..10 = c, 9..7 = v, 6 = h, 5..1 = l, 0 = q; every shared-memory and
-// global access of a warp is 512 contiguous bytes.  The halving tree reduces
-// bits from the top down:
+// global access of a warp is 512 contiguous bytes.  The halving tree:
 //   - bits 12..10 in the thread: the producer copies the chunks in bit-
-//     reversed order (0, 4, 2, 6, 1, 5, 3, 7), so each tree node is complete
-//     as soon as its second half arrives and three partial vectors suffice;
+//     reversed order (0, 4, 2, 6, 1, 5, 3, 7), so consecutive chunk pairs
+//     are the tree's first level and their four sums, kept in order, its
+//     next two;
 //   - bits 9..7 across warps: every warp writes its four node values to one
 //     of two exchange slots (an mbarrier pair per slot, so no warp waits for
 //     the others except through a bounded wait), and one warp, rotating with
 //     the tile, finishes the tile: bits 9..7, then bit 6 in the thread,
 //     bits 5..1 by warp shuffles, bit 0 in lane 0.
 // The last tile, when n is not a multiple of 8192, is read from global memory
-// by the same threads in the same order, +0 past n.  Loads never wait on
-// compute: the ring keeps up to S - 1 stages in flight.  Every mbarrier wait is
+// by the same threads in the same order, +0 past n.  Every mbarrier wait is
 // bounded (bulk.cuh); one that runs out ends the kernel and is reported by
 // wxpy_reduce_status().
-//
-// Element path (other alignments).  A block of 256 threads takes a tile;
-// thread t owns elements 1024k + 4t + q (k = 0..7, q = 0..3): bits 12..10 in
-// the thread, 9..7 across warps through shared memory, 6..2 by shuffles, 1..0
-// in lane 0, each element read and written on its own.
 //
 // Either way the tile sums go to a workspace, and the last block to finish
 // (an atomic ticket, no waiting) sums them with the same tree.
@@ -45,10 +49,11 @@
 // Pipes: per element two products (alpha*x and the term) and, on average, two
 // sums (the update's and one tree level).  A share of the tiles (mul_sixteenths,
 // by a rotation over blocks and tile iterations) computes both products in the
-// integer pipelines (fp64_mul.cuh); the sums stay in FP64.  The choice is made
-// once per tile between two instantiated bodies: a choice per element slot was
-// if-converted by the compiler, which then issued the FP64 body, predicated
-// off, for the integer-pipeline slots too.  The bits are the same either way.
+// integer pipelines (fp64_mul.cuh).  The choice is made once per tile between
+// two instantiated bodies: a choice per element slot was if-converted by the
+// compiler, which then issued the FP64 body, predicated off, for the
+// integer-pipeline slots too.  The bits are the same for every configuration;
+// wxpy_reduce_tune searches them (reduce_tune.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
