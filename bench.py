@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -448,10 +449,20 @@ def tune_buckets(wx, args, torch):
             "seconds": time.perf_counter() - t0, "buckets": rows}
 
 
+def flushed_batch(n):
+    """Calls per flushed timing of an n-element call: the device's event
+    timestamps advance in 2.048 us steps on GB300, so a call expected to take
+    under 200 us is timed as a batch of back-to-back calls on disjoint slices
+    of the vectors (each slice cold after the flush), divided by its length."""
+    est_us = 24.0 * n / 6.0e6 + 3.0
+    return 1 if est_us >= 200.0 else int(min(64, math.ceil(200.0 / est_us)))
+
+
 def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=9):
     """GB/s per n: median of ``reps`` with the L2 flushed (read of a 512 MB buffer)
-    before each timed call, and L2-resident (back-to-back) for n <= 2^22.  A
-    device sleep is queued ahead of each timed call so that the host's launch
+    before each timed run -- one call, or a batch of calls on disjoint slices for
+    short calls (flushed_batch) -- and L2-resident (back-to-back) for n <= 2^22.
+    A device sleep is queued ahead of each timed run so that the host's launch
     latency is not part of the device time."""
     flush = torch.empty(64 << 20, dtype=torch.float64, device=x.device)
     flush.fill_(1.0)
@@ -459,18 +470,24 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
     px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
     for (n, o) in calls:
         args = (n, alpha, px + 8 * o, py + 8 * o, pw + 8 * o, sh)
+        b = flushed_batch(n)
+        stride = (n + 64 + 31) // 32 * 32  # elements: 256-byte steps keep the offset class
+        assert b == 1 or o + (b - 1) * stride + n <= x.numel()
+        batch = [(n, alpha, px + 8 * (o + i * stride), py + 8 * (o + i * stride),
+                  pw + 8 * (o + i * stride), sh) for i in range(b)]
         tf = []
         for _ in range(reps):
             flush.sum()
-            torch.cuda._sleep(100000)
+            torch.cuda._sleep(100000 + 30000 * b)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lib.wxpy(*args)
+            for a in batch:
+                lib.wxpy(*a)
             e1.record(stream)
             e1.synchronize()
-            tf.append(e0.elapsed_time(e1))
-        row = {"n": n, "offset_bytes": 8 * o,
+            tf.append(e0.elapsed_time(e1) / b)
+        row = {"n": n, "offset_bytes": 8 * o, "calls_per_flushed_run": b,
                "gbs_l2_flushed": BYTES_PER_ELEM * n / (statistics.median(tf) / 1e3) / 1e9,
                "us_l2_flushed": statistics.median(tf) * 1e3}
         if n <= (1 << 22) + 3:

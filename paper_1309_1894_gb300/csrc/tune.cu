@@ -17,8 +17,14 @@
 //   B. threads per block x grid mode, from the best of A;
 //   C. carveout x stream count, from the best of B.
 // Each candidate is timed `reps` times; the median counts.  Before every timed
-// run the L2 is flushed by reading a buffer of twice its size, and a short
-// device delay is queued first so that the host's launch latency is not timed.
+// run the L2 is flushed by reading a buffer of twice its size, and a device
+// delay is queued first so that the host's launch latency is not timed.  The
+// device's event timestamps advance in steps of 2.048 us on GB300 (every
+// elapsed time of the size sweep is a multiple of it), so a call expected to
+// take under 200 us is timed as a batch of back-to-back calls, each on its own
+// copy of the inputs in an arena laid out like the tuning buffers (same
+// alignment class, none of the copies in L2 after the flush), and the batch
+// time is divided by its length.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +52,9 @@ __global__ void delay_kernel(long long cycles) {
 
 struct Scratch {
     double *x = nullptr, *y = nullptr, *x0 = nullptr, *wref = nullptr, *wcand = nullptr;
+    double *arena = nullptr;  // batch copies: `batch` sets of x, y, w, each `set_elems` long
+    int64_t set_elems = 0, y_off = 0, w_off = 0;
+    int batch = 1;
     void *flush = nullptr;
     int64_t flush_bytes = 0;
     unsigned long long *count = nullptr;
@@ -53,8 +62,8 @@ struct Scratch {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ~Scratch() {
         if (s) cudaStreamSynchronize(s);
-        for (void *p : {(void *)x, (void *)y, (void *)x0, (void *)wref, (void *)wcand, flush,
-                        (void *)count})
+        for (void *p : {(void *)x, (void *)y, (void *)x0, (void *)wref, (void *)wcand,
+                        (void *)arena, flush, (void *)count})
             if (p) cudaFree(p);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -81,26 +90,58 @@ int alloc(void **p, size_t bytes) {
     return WXPY_OK;
 }
 
-// Median device time (us) of `reps` runs of variant v.
-int time_variant(const Variant &v, const Problem &p, Scratch &sc, int reps, bool flush,
-                 double *median_us) {
+// Median device time (us per call) of `reps` timed runs; each run is one
+// call, or sc.batch back-to-back calls launch(0 .. batch-1) divided by batch.
+template <class Launch>
+int time_calls(Scratch &sc, int reps, bool flush, Launch &&launch, double *median_us) {
     std::vector<float> ms(reps);
     for (int r = 0; r < reps; ++r) {
         int st;
         if (flush && (st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK)
             return st;
-        delay_kernel<<<1, 1, 0, sc.s>>>(20000);
+        // long enough to cover the host's enqueueing of the whole batch
+        delay_kernel<<<1, 1, 0, sc.s>>>(20000 + 10000ll * sc.batch);
         cudaEventRecord(sc.e0, sc.s);
-        st = run_variant(v, p.cls, p.n, p.alpha, p.x, p.y, p.w, sc.s);
-        if (st != WXPY_OK) return st;
+        for (int i = 0; i < sc.batch; ++i)
+            if ((st = launch(i)) != WXPY_OK) return st;
         cudaEventRecord(sc.e1, sc.s);
         cudaError_t e = cudaEventSynchronize(sc.e1);
         if (e != cudaSuccess) return fail_cuda(e, "tuner timing");
         cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
     }
     std::sort(ms.begin(), ms.end());
-    *median_us = 1e3 * (double)ms[reps / 2];
+    *median_us = 1e3 * (double)ms[reps / 2] / sc.batch;
     return WXPY_OK;
+}
+
+// The operands of call i of a batch: the tuning buffers themselves for one
+// call or resident timing, else copy i in the arena (same offsets within a
+// 256-byte-aligned set, so the same alignment and alias class).
+void batch_operands(const Problem &p, const Scratch &sc, bool flush, int i, const double **x,
+                    const double **y, double **w) {
+    if (sc.batch == 1 || !flush) {
+        *x = p.x;
+        *y = p.y;
+        *w = p.w;
+        return;
+    }
+    double *base = sc.arena + (int64_t)i * sc.set_elems;
+    const int64_t xo = (const char *)p.x - (const char *)sc.x;  // off_x bytes
+    double *xi = (double *)((char *)base + xo);
+    *x = xi;
+    *y = p.y == p.x ? xi : base + sc.y_off;
+    *w = p.w == p.x ? xi : base + sc.w_off;
+}
+
+// Median device time (us per call) of `reps` runs of variant v.
+int time_variant(const Variant &v, const Problem &p, Scratch &sc, int reps, bool flush,
+                 double *median_us) {
+    return time_calls(sc, reps, flush, [&](int i) {
+        const double *x, *y;
+        double *w;
+        batch_operands(p, sc, flush, i, &x, &y, &w);
+        return run_variant(v, p.cls, p.n, p.alpha, x, y, w, sc.s);
+    }, median_us);
 }
 
 // Runs v once on pristine inputs and counts bit mismatches against wref.
@@ -186,9 +227,26 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
         if (e != cudaSuccess) return fail_cuda(e, "tuner reference run");
     }
     // Repetitions: more for short runs, whose times are noisier.
-    const double est_us = 24.0 * (double)n / 6.0e3 + 3.0;
+    const double est_us = 24.0 * (double)n / 6.0e6 + 3.0;  // 6 TB/s = 6e6 bytes per us
     int reps = est_us > 2000 ? 5 : (est_us > 200 ? 7 : 11);
     if (quick) reps = std::max(3, reps / 2);
+    // Batches of back-to-back calls for short ones (at least about 200 us per
+    // timed run), within a 2 GiB arena when each call needs its own copy.
+    if (est_us < 200.0) {
+        const int64_t vb = ((int64_t)n * 8 + 64 + 255) / 256 * 256;
+        sc.set_elems = 3 * vb / 8;
+        sc.y_off = vb / 8;
+        sc.w_off = 2 * vb / 8;
+        int b = (int)std::min(64.0, std::ceil(200.0 / est_us));
+        if (flush) b = (int)std::min<int64_t>(b, ((int64_t)2 << 30) / (3 * vb));
+        sc.batch = std::max(1, b);
+        if (flush && sc.batch > 1) {
+            if ((st = alloc((void **)&sc.arena, (size_t)(sc.batch * 3 * vb)))) return st;
+            if ((st = launch_fill_uniform(sc.arena, sc.batch * sc.set_elems, 20130907ull, 3, 0, -1.0,
+                                          1.0, sc.s)))
+                return st;
+        }
+    }
 
     int candidates = 0, rejected = 0;
     auto consider = [&](const Variant &raw, std::vector<Candidate> &pool) -> int {
@@ -255,22 +313,15 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
     if ((st = time_variant(best.v, p, sc, reps, flush, &best_us)) != WXPY_OK) return st;
     const Variant dv = default_variant(p.cls, n);
     if ((st = time_variant(dv, p, sc, reps, flush, &def_us)) != WXPY_OK) return st;
-    {
-        std::vector<float> ms(reps);
-        for (int r = 0; r < reps; ++r) {
-            if (flush && (st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s))) return st;
-            delay_kernel<<<1, 1, 0, sc.s>>>(20000);
-            cudaEventRecord(sc.e0, sc.s);
-            SingleArgs a{p.x, p.y, p.w, p.alpha, n, 0, 0};
-            e = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
-            if (e != cudaSuccess) return fail_cuda(e, "tuner reference timing");
-            cudaEventRecord(sc.e1, sc.s);
-            if ((e = cudaEventSynchronize(sc.e1)) != cudaSuccess) return fail_cuda(e, "tuner sync");
-            cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
-        }
-        std::sort(ms.begin(), ms.end());
-        ref_us = 1e3 * (double)ms[reps / 2];
-    }
+    st = time_calls(sc, reps, flush, [&](int i) {
+        const double *x, *y;
+        double *w;
+        batch_operands(p, sc, flush, i, &x, &y, &w);
+        SingleArgs a{x, y, w, p.alpha, n, 0, 0};
+        const cudaError_t le = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
+        return le == cudaSuccess ? WXPY_OK : fail_cuda(le, "tuner reference timing");
+    }, &ref_us);
+    if (st != WXPY_OK) return st;
     // Keep whichever of the winner and the default is faster on the re-timing.
     Variant chosen = best.v;
     double chosen_us = best_us;
