@@ -273,7 +273,8 @@ typedef struct wxpy_vecops_tune_result {
  * 0, 2, .., 16 sixteenths with the sums in FP64; then the sums every other or
  * all in the integer pipeline at the best product share) is run once from
  * pristine inputs and compared with it bit for bit -- a single differing bit
- * rejects it -- and timed as the median of five runs, each after an L2 flush.
+ * rejects it -- and timed as the median of five runs of three back-to-back
+ * calls, each run after an L2 flush.
  * The fastest verified split becomes the class's split for later calls that
  * leave wxpy_vecops_pipes at -1, and is saved and loaded with the tune cache
  * (wxpy_tune_cache_save / _load).  `results` (WXPY_VEC_CLASSES entries) may
@@ -371,7 +372,7 @@ typedef struct wxpy_reduce_tune_result {
  * levels at the best share and at half of it; the three staged shapes at the
  * best share) is run once and compared with it bit for bit -- a single
  * differing bit of w or of the result rejects it -- and timed as the median
- * of five runs, each after an L2 flush.  The fastest verified configuration
+ * of five runs of three back-to-back calls, each run after an L2 flush.  The fastest verified configuration
  * becomes the operation's configuration for later calls whose knobs are left
  * at -1, and is saved and loaded with the tune cache.  `results` (2 entries)
  * may be NULL.  Allocates about 5 n doubles of scratch while it runs, on the
@@ -507,13 +508,16 @@ typedef struct wxpy_tune_result {
 } wxpy_tune_result;
 
 /* Runs the search of Sec. 2 for the cell of size bucket floor(log2 n) and the
- * class selected by `flags`: it allocates its own scratch (about 4 * 8n bytes
- * plus a buffer of twice the L2 size), fills the inputs from the seeded
+ * class selected by `flags`: it allocates its own scratch (about 4 * 8n bytes,
+ * a buffer of twice the L2 size, and for calls expected under 200 us an arena
+ * of at most 2 GiB of input copies), fills the inputs from the seeded
  * generator, runs the reference variant once, then runs every candidate
  * (coordinate search: width x unroll x cache, then threads x grid mode, then
  * carveout x streams), rejects any whose output differs from the reference
  * results by a single bit, times the rest with CUDA events (median of several
- * runs, L2 flushed before each), and stores the fastest -- or the default
+ * runs, L2 flushed before each; a call expected under 200 us is timed as a
+ * batch of back-to-back calls on separate copies of the inputs, below the
+ * event clock's 2.048 us step), and stores the fastest -- or the default
  * variant, if it re-times faster -- in the tuning table, where every later
  * wxpy() call of that cell finds it.  Synchronous; serialised by a mutex;
  * frees its scratch before returning.  `out` may be NULL.

@@ -12,9 +12,10 @@
 // configuration whose w or result differs by a single bit is rejected.
 // Candidates, per operation: the register-loaded form at product shares 0, 4,
 // .., 16 sixteenths; for norm2, one to three integer tree levels at the best
-// share and at half of it; the three staged shapes at the best share.  Timing
-// as in tune.cu: median of five runs, each after an L2 flush and a short
-// device delay (w never aliases an input here, so no restore is needed).
+// share and at half of it; the three staged shapes at the best share.  Timing:
+// median of five runs of three back-to-back calls, each run after an L2 flush
+// and a short device delay (w never aliases an input here, so no restore is
+// needed).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,21 +71,27 @@ int run_once(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *w, doubl
                       sc.ws_bytes, c, sc.s);
 }
 
+// Median device time (us per call) of kReps timed runs, each kBatch back-to-
+// back calls (the event timestamps advance in 2.048 us steps on GB300; the
+// operands exceed the L2, so every call reads them from memory).
+constexpr int kBatch = 3;
+
 int time_config(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *median_us) {
     std::vector<float> ms(kReps);
     for (int r = 0; r < kReps; ++r) {
         int st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
-        rtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000);
+        rtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000 * kBatch);
         cudaEventRecord(sc.e0, sc.s);
-        if ((st = run_once(kind, n, c, sc, sc.w, sc.res)) != WXPY_OK) return st;
+        for (int b = 0; b < kBatch; ++b)
+            if ((st = run_once(kind, n, c, sc, sc.w, sc.res)) != WXPY_OK) return st;
         cudaEventRecord(sc.e1, sc.s);
         cudaError_t e = cudaEventSynchronize(sc.e1);
         if (e != cudaSuccess) return fail_cuda(e, "reduction tuner timing");
         cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
     }
     std::sort(ms.begin(), ms.end());
-    *median_us = 1e3 * (double)ms[kReps / 2];
+    *median_us = 1e3 * (double)ms[kReps / 2] / kBatch;
     return WXPY_OK;
 }
 

@@ -9,9 +9,10 @@
 // of the all-FP64 split on the same inputs; a split whose output differs by a
 // single bit is rejected.  Candidates per class: the product share 0, 2, ..,
 // 16 sixteenths with the sums in FP64, then the sums every other one or all
-// in the integer pipeline at the best product share.  Timing as in tune.cu:
-// median of five runs, each after an L2 flush and a short device delay, with
-// the in-place output restored from a pristine copy before every run.
+// in the integer pipeline at the best product share.  Timing: median of five
+// runs of three back-to-back calls, each run after an L2 flush and a short
+// device delay, with the in-place output restored from a pristine copy before
+// every run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,22 +103,31 @@ int restore(const ClassCall &c, int64_t n, VScratch &sc) {
     return e == cudaSuccess ? WXPY_OK : fail_cuda(e, "vector tuner restore");
 }
 
+// Median device time (us per call) of kReps timed runs, each kBatch back-to-
+// back calls: the event timestamps advance in 2.048 us steps on GB300, about
+// 3 % of one call at the search's size, and the operands of every class
+// exceed the L2, so each call of a run reads them from memory.  The in-place
+// output is restored before each run only (the coefficients keep a few
+// repeated applications in range).
+constexpr int kBatch = 3;
+
 int time_split(const ClassCall &c, int64_t n, VecPipes p, VScratch &sc, double *median_us) {
     std::vector<float> ms(kReps);
     for (int r = 0; r < kReps; ++r) {
         int st;
         if ((st = restore(c, n, sc)) != WXPY_OK) return st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
-        vtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000);
+        vtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000 * kBatch);
         cudaEventRecord(sc.e0, sc.s);
-        if ((st = vecops_run(c.cls, n, kCoef, c.in, c.out, p, sc.s)) != WXPY_OK) return st;
+        for (int b = 0; b < kBatch; ++b)
+            if ((st = vecops_run(c.cls, n, kCoef, c.in, c.out, p, sc.s)) != WXPY_OK) return st;
         cudaEventRecord(sc.e1, sc.s);
         cudaError_t e = cudaEventSynchronize(sc.e1);
         if (e != cudaSuccess) return fail_cuda(e, "vector tuner timing");
         cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
     }
     std::sort(ms.begin(), ms.end());
-    *median_us = 1e3 * (double)ms[kReps / 2];
+    *median_us = 1e3 * (double)ms[kReps / 2] / kBatch;
     return WXPY_OK;
 }
 
