@@ -111,6 +111,15 @@ int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s) 
     return WXPY_OK;
 }
 
+__global__ void device_delay_kernel(long long cycles) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < cycles) __nanosleep(500);
+}
+
+void launch_device_delay(long long cycles, cudaStream_t s) {
+    device_delay_kernel<<<1, 1, 0, s>>>(cycles);
+}
+
 }  // namespace wx
 
 using namespace wx;

@@ -31,11 +31,6 @@ namespace {
 
 std::mutex g_rtune_mu;
 
-__global__ void rtune_delay_kernel(long long cycles) {
-    const long long t0 = clock64();
-    while (clock64() - t0 < cycles) __nanosleep(500);
-}
-
 constexpr int kReps = 5;
 constexpr double kAlpha = -0.625;
 
@@ -81,7 +76,7 @@ int time_config(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *media
     for (int r = 0; r < kReps; ++r) {
         int st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
-        rtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000 * kBatch);
+        launch_device_delay(20000 * kBatch, sc.s);
         cudaEventRecord(sc.e0, sc.s);
         for (int b = 0; b < kBatch; ++b)
             if ((st = run_once(kind, n, c, sc, sc.w, sc.res)) != WXPY_OK) return st;

@@ -45,11 +45,6 @@ namespace {
 
 std::mutex g_tune_mu;
 
-__global__ void delay_kernel(long long cycles) {
-    const long long t0 = clock64();
-    while (clock64() - t0 < cycles) __nanosleep(500);
-}
-
 struct Scratch {
     double *x = nullptr, *y = nullptr, *x0 = nullptr, *wref = nullptr, *wcand = nullptr;
     double *arena = nullptr;  // batch copies: `batch` sets of x, y, w, each `set_elems` long
@@ -100,7 +95,7 @@ int time_calls(Scratch &sc, int reps, bool flush, Launch &&launch, double *media
         if (flush && (st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK)
             return st;
         // long enough to cover the host's enqueueing of the whole batch
-        delay_kernel<<<1, 1, 0, sc.s>>>(20000 + 10000ll * sc.batch);
+        launch_device_delay(20000 + 10000ll * sc.batch, sc.s);
         cudaEventRecord(sc.e0, sc.s);
         for (int i = 0; i < sc.batch; ++i)
             if ((st = launch(i)) != WXPY_OK) return st;

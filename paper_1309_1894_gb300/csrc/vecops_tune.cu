@@ -27,11 +27,6 @@ namespace {
 
 std::mutex g_vtune_mu;
 
-__global__ void vtune_delay_kernel(long long cycles) {
-    const long long t0 = clock64();
-    while (clock64() - t0 < cycles) __nanosleep(500);
-}
-
 constexpr int kMaxVecs = 9;  // inputs of the widest class (maxpy with 8 terms)
 constexpr int kReps = 5;
 constexpr double kCoef[8] = {0.75, -1.5, 1.25, -0.625, 1.875, -0.3125, 0.5625, -1.0625};
@@ -117,7 +112,7 @@ int time_split(const ClassCall &c, int64_t n, VecPipes p, VScratch &sc, double *
         int st;
         if ((st = restore(c, n, sc)) != WXPY_OK) return st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
-        vtune_delay_kernel<<<1, 1, 0, sc.s>>>(20000 * kBatch);
+        launch_device_delay(20000 * kBatch, sc.s);
         cudaEventRecord(sc.e0, sc.s);
         for (int b = 0; b < kBatch; ++b)
             if ((st = vecops_run(c.cls, n, kCoef, c.in, c.out, p, sc.s)) != WXPY_OK) return st;
