@@ -308,8 +308,13 @@ def _prepare(alpha, x, y, w):
     return n, float(alpha), px, py, pw, w
 
 
-def wxpy(alpha: float, x, y, w=None, stream=None):
-    """w = alpha*x + y (FP64, no FMA) on ``stream``; returns w (allocated if None)."""
+def wxpy(alpha: float, x, y, w=None, stream=None, *, out=None):
+    """w = alpha*x + y (FP64, no FMA) on ``stream``; returns w (allocated if
+    None).  ``out`` is another name for ``w``."""
+    if out is not None:
+        if w is not None and w is not out:
+            raise ValueError("give w or out, not both")
+        w = out
     n, a, px, py, pw, w = _prepare(alpha, x, y, w)
     check(lib().wxpy(n, a, px, py, pw, _stream_handle(stream)), "wxpy")
     return w
@@ -566,6 +571,11 @@ def wxpy_tune(n: int, flags: int = 0) -> dict:
     r = TuneResult()
     check(lib().wxpy_tune(n, flags, ctypes.byref(r)), "wxpy_tune")
     return r.as_dict()
+
+
+def tune(n: int, flags: int = 0) -> dict:
+    """The Sec. 2 search for the size bucket of n (see wxpy_tune)."""
+    return wxpy_tune(n, flags)
 
 
 def wxpy_tune_get(tune_key: int) -> int:

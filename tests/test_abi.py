@@ -218,3 +218,15 @@ def test_reduce_validation_before_cuda(lib):
     assert lib.wxpy_reduce_pipes(17) == wx.WXPY_EINVAL
     assert lib.wxpy_reduce_pipes(-2) == wx.WXPY_EINVAL
     assert lib.wxpy_reduce_pipes(-1) == 0
+
+
+def test_python_surface_names():
+    """The Python names of the package's public surface: wxpy(alpha, x, y, out=...),
+    tune(n) and Server, with no GPU call."""
+    import inspect
+    sig = inspect.signature(wx.wxpy)
+    assert list(sig.parameters)[:3] == ["alpha", "x", "y"] and "out" in sig.parameters
+    assert wx.tune.__doc__ and callable(wx.tune)
+    assert inspect.isclass(wx.Server)
+    with pytest.raises(ValueError):
+        wx.wxpy(1.0, None, None, w=object(), out=object())
