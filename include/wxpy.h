@@ -147,7 +147,10 @@ int wxpy_variant_encode(const wxpy_variant_info *v, int *id);
 
 /* Forces every later wxpy() call of the process to use variant `id`
  * (tests, benchmarks); id = -1 restores the normal lookup (tuned entry, else
- * the built-in default). */
+ * the built-in default).  The environment variable WXPY_FORCE_VARIANT=<id>
+ * forces a variant from the process's start, as if this had been called
+ * first (read once; a value that is not a valid id is ignored); a later call
+ * of this function still wins. */
 int wxpy_set_variant(int id);
 
 /* Reports in *out the variant that wxpy(n, ., x, y, w, .) would launch now,
@@ -524,6 +527,10 @@ typedef struct wxpy_tune_result {
  * Errors: WXPY_EINVAL (n <= 0, XY with WALIAS), WXPY_ENOMEM, WXPY_ECUDA,
  * WXPY_EMISMATCH (no candidate matched the reference). */
 int wxpy_tune(int64_t n, unsigned flags, wxpy_tune_result *out);
+/* For this search and the other two (wxpy_vecops_tune, wxpy_reduce_tune), the
+ * environment variable WXPY_TUNE_REPS=<1..101> sets the timed runs per
+ * candidate, whose median counts (read at every search; other values are
+ * ignored). */
 
 /* The tuning table: one variant id per cell (tune_key of wxpy_class_info),
  * -1 for an untuned cell.  get/set/clear touch no device; clear also drops

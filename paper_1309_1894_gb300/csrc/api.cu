@@ -444,15 +444,34 @@ int wxpy_variant_encode(const wxpy_variant_info *v, int *id) {
     return WXPY_OK;
 }
 
+// WXPY_FORCE_VARIANT: a variant id forced from the process's start, as if
+// wxpy_set_variant had been called first (read once; a value that is not a
+// valid id is ignored).  An explicit wxpy_set_variant call still wins.
+static std::once_flag g_force_env_once;
+
+static void read_force_env() {
+    std::call_once(g_force_env_once, [] {
+        const char *s = std::getenv("WXPY_FORCE_VARIANT");
+        if (!s || !*s) return;
+        char *end = nullptr;
+        const long id = std::strtol(s, &end, 10);
+        if (*end != '\0' || id < 0 || id >= kVariantCount) return;
+        int expected = -1;
+        g_forced_variant.compare_exchange_strong(expected, (int)id);
+    });
+}
+
 int wxpy_set_variant(int id) {
     if (id != -1 && (id < 0 || id >= kVariantCount))
         return fail(WXPY_EINVAL, "variant id %d out of range", id);
+    read_force_env();
     g_forced_variant.store(id);
     return WXPY_OK;
 }
 
 static int select_variant(const CallClass &c, int64_t n, Variant *v, int *source) {
     autoload_tune_cache();
+    read_force_env();
     const int forced = g_forced_variant.load(std::memory_order_relaxed);
     if (forced >= 0 && decode_variant(forced, v)) {
         *source = 2;

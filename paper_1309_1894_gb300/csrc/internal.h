@@ -120,6 +120,9 @@ int launch_fill_uniform(double *dst, int64_t n, uint64_t seed, uint32_t tag, int
 int launch_count_mismatch(const double *a, const double *b, int64_t n,
                           unsigned long long *count_dev, cudaStream_t s);
 int launch_l2_flush(const void *buf, int64_t bytes, void *sink, cudaStream_t s);
+// Timed runs per candidate of a search: WXPY_TUNE_REPS (1..101) when set,
+// else `fallback` (tune.cu).
+int tune_reps(int fallback);
 // A one-thread kernel that spins for `cycles` SM clocks: queued ahead of a
 // timed region so that the host's launch latency is not timed.
 void launch_device_delay(long long cycles, cudaStream_t s);

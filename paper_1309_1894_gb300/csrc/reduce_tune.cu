@@ -72,8 +72,9 @@ int run_once(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *w, doubl
 constexpr int kBatch = 3;
 
 int time_config(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *median_us) {
-    std::vector<float> ms(kReps);
-    for (int r = 0; r < kReps; ++r) {
+    const int reps = tune_reps(kReps);
+    std::vector<float> ms(reps);
+    for (int r = 0; r < reps; ++r) {
         int st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
         launch_device_delay(20000 * kBatch, sc.s);
@@ -86,7 +87,7 @@ int time_config(int kind, int64_t n, ReduceConfig c, RScratch &sc, double *media
         cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
     }
     std::sort(ms.begin(), ms.end());
-    *median_us = 1e3 * (double)ms[kReps / 2] / kBatch;
+    *median_us = 1e3 * (double)ms[reps / 2] / kBatch;
     return WXPY_OK;
 }
 

@@ -225,6 +225,7 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
     const double est_us = 24.0 * (double)n / 6.0e6 + 3.0;  // 6 TB/s = 6e6 bytes per us
     int reps = est_us > 2000 ? 5 : (est_us > 200 ? 7 : 11);
     if (quick) reps = std::max(3, reps / 2);
+    reps = tune_reps(reps);
     // Batches of back-to-back calls for short ones (at least about 200 us per
     // timed run), within a 2 GiB arena when each call needs its own copy.
     if (est_us < 200.0) {
@@ -581,6 +582,14 @@ std::string current_device_key(int *status) {
 
 namespace {
 std::once_flag g_autoload_once;
+}
+
+int tune_reps(int fallback) {
+    const char *s = std::getenv("WXPY_TUNE_REPS");
+    if (!s || !*s) return fallback;
+    char *end = nullptr;
+    const long v = std::strtol(s, &end, 10);
+    return (*end == '\0' && v >= 1 && v <= 101) ? (int)v : fallback;
 }
 
 void autoload_tune_cache() {

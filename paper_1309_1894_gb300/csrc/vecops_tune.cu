@@ -107,8 +107,9 @@ int restore(const ClassCall &c, int64_t n, VScratch &sc) {
 constexpr int kBatch = 3;
 
 int time_split(const ClassCall &c, int64_t n, VecPipes p, VScratch &sc, double *median_us) {
-    std::vector<float> ms(kReps);
-    for (int r = 0; r < kReps; ++r) {
+    const int reps = tune_reps(kReps);
+    std::vector<float> ms(reps);
+    for (int r = 0; r < reps; ++r) {
         int st;
         if ((st = restore(c, n, sc)) != WXPY_OK) return st;
         if ((st = launch_l2_flush(sc.flush, sc.flush_bytes, sc.count, sc.s)) != WXPY_OK) return st;
@@ -122,7 +123,7 @@ int time_split(const ClassCall &c, int64_t n, VecPipes p, VScratch &sc, double *
         cudaEventElapsedTime(&ms[r], sc.e0, sc.e1);
     }
     std::sort(ms.begin(), ms.end());
-    *median_us = 1e3 * (double)ms[kReps / 2] / kBatch;
+    *median_us = 1e3 * (double)ms[reps / 2] / kBatch;
     return WXPY_OK;
 }
 

@@ -230,3 +230,38 @@ def test_python_surface_names():
     assert inspect.isclass(wx.Server)
     with pytest.raises(ValueError):
         wx.wxpy(1.0, None, None, w=object(), out=object())
+
+
+@pytest.mark.parametrize("value,forced", [("4112", True), ("-3", False), ("12x", False),
+                                          ("99999999", False)])
+def test_force_variant_from_environment(value, forced):
+    """WXPY_FORCE_VARIANT forces the lookup from the process's start (no GPU
+    call: the lookup classifies pointer values); invalid values are ignored,
+    and an explicit wxpy_set_variant(-1) still wins."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import ctypes, sys
+import paper_1309_1894_gb300 as wx
+lib = wx.lib()
+info = wx.binding.VariantInfo()
+src = ctypes.c_int()
+base = 1 << 40
+assert lib.wxpy_lookup(1 << 20, base, base + (1 << 24), base + (2 << 24), ctypes.byref(info),
+                       ctypes.byref(src)) == 0
+first = src.value
+assert lib.wxpy_set_variant(-1) == 0
+assert lib.wxpy_lookup(1 << 20, base, base + (1 << 24), base + (2 << 24), ctypes.byref(info),
+                       ctypes.byref(src)) == 0
+print(first, src.value)
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WXPY_FORCE_VARIANT=value, PYTHONPATH=root)
+    env.pop("WXPY_TUNE_CACHE", None)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    first, after = (int(t) for t in r.stdout.split())
+    assert first == (2 if forced else 0)
+    assert after == 0

@@ -112,7 +112,8 @@ def test_tuned_sweep_parity():
 
 def test_traced_paths_run_with_nvtx_on():
     """With WXPY_NVTX=1 (ranges around the searches, batched launches and
-    server batches) the traced paths still run and give the oracle's bits.
+    server batches) and WXPY_TUNE_REPS=3 the traced paths still run and give
+    the oracle's bits.
     A subprocess, since the setting is read once per process."""
     import os
     import subprocess
@@ -135,7 +136,7 @@ wx.wxpy_vecops_tune(1 << 14)
 print("traced ok")
 '''
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, WXPY_NVTX="1", PYTHONPATH=root)
+    env = dict(os.environ, WXPY_NVTX="1", WXPY_TUNE_REPS="3", PYTHONPATH=root)
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "traced ok" in r.stdout, r.stderr[-2000:]
