@@ -419,9 +419,47 @@ def run_ours(args):
             "all_cores": {"value": rate_all, "cores": cores,
                           "how": "each call split into contiguous chunks, one thread each"}}
         print(json.dumps(result), flush=True)
+        if args.jsonl:
+            write_jsonl(args.jsonl, result)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def case_rows(obj, path, common):
+    """One row per measured case of the bench line: every list of records under
+    ``path`` becomes rows tagged ``"case": path``; scalars of a record stay in
+    its row, nested records and lists are followed."""
+    rows = []
+    if isinstance(obj, list):
+        for item in obj:
+            if isinstance(item, dict):
+                row = {"case": path, **common}
+                row.update({k: v for k, v in item.items() if not isinstance(v, (dict, list))})
+                rows.append(row)
+                for k, v in item.items():
+                    if isinstance(v, (dict, list)):
+                        rows += case_rows(v, f"{path}.{k}", common)
+    elif isinstance(obj, dict):
+        flat = {k: v for k, v in obj.items() if not isinstance(v, (dict, list))}
+        if flat:
+            rows.append({"case": path, **common, **flat})
+        for k, v in obj.items():
+            if isinstance(v, (dict, list)):
+                rows += case_rows(v, f"{path}.{k}" if path else k, common)
+    return rows
+
+
+def write_jsonl(path, result):
+    """Writes the bench line's cases as JSON lines (one measured case each)."""
+    common = {"metric": result.get("metric"), "n_gpus": result.get("n_gpus"),
+              "time": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    rows = case_rows(result, "", common)
+    with open(path, "a") as f:
+        for r in rows:
+            if r["case"] == "":
+                r["case"] = "step"
+            f.write(json.dumps(r) + "\n")
 
 
 def tune_buckets(wx, args, torch):
@@ -891,6 +929,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--jsonl", default=None,
+                    help="also append one JSON line per measured case to this file")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-n sweep and stream-split measurements")
