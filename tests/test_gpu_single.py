@@ -197,6 +197,35 @@ def test_every_variant_family_member(alias, off):
             g.check()
 
 
+
+@pytest.mark.parametrize("alias", ["none", "x=y"])
+def test_every_compiled_instance_forced(alias):
+    """Every compiled kernel instance, forced through wxpy_run_variant on
+    32-byte co-aligned pointers (so nothing narrows the vector width): vector
+    width x unroll x grid mode x cache policy x fp64_offload, with distinct x
+    and y or x == y (the template's x == y argument), at a ragged n that has a
+    head-free body, several unrolled passes and a tail."""
+    enc = wx.wxpy_variant_encode
+    n = 3 * 4096 + 37
+    alpha, (x, y, w), (xh, yh), want, guards = make_case(n, 0, alias, synth.BASE_SEED + 77)
+    count = 0
+    for vb in (8, 16, 32):
+        for u in (1, 2, 4, 8):
+            for bps in (0, 2):  # one-shot grid, grid-stride
+                for c in (0, 1, 2):
+                    for of in (0, 1, 2):
+                        vid = enc(vec_bytes=vb, unroll=u, threads=256, blocks_per_sm=bps,
+                                  cache=c, carveout=-1, streams=1, fp64_offload=of)
+                        w.fill_(7.0)
+                        wx.wxpy_run_variant(vid, alpha, x, y, w)
+                        torch.cuda.synchronize()
+                        ok, msg = bits_equal(w, want)
+                        assert ok, (vb, u, bps, c, of, msg)
+                        count += 1
+    for g in guards:
+        g.check()
+    assert count == 216
+
 @pytest.mark.parametrize("alias", ALIASES)
 def test_tiny_sizes_exhaustive(alias):
     """n = 0..67 at every 8-byte offset, default lookup and reference variant."""
