@@ -946,7 +946,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="profiling mode: force this variant id instead of the tuned one")
     ap.add_argument("--vecop", default="",
-                    help="profiling mode: only run this kernel (axpbypcz, axpby, maxpy4, maxpy8, "
+                    help="profiling mode: only run this kernel (batch: SINGLE segments; axpbypcz, axpby, maxpy4, maxpy8, "
                          "pointwise_mult, norm2, dot; serve: one 64-request server batch with "
                          "n up to SINGLE) on n = SINGLE, --reps times")
     ap.add_argument("--pipes", default="-1,-1",
@@ -996,6 +996,27 @@ def run_vecop(args):
     import paper_1309_1894_gb300 as wx
     from paper_1309_1894_gb300 import synth
     n = args.single
+    if args.vecop == "batch":
+        # one persistent segmented launch: SINGLE segments, n log-uniform in [1, 2^20]
+        seed = synth.BASE_SEED + 3
+        ns = synth.log_uniform_lengths(seed, n, 1, 1 << 20)
+        starts, total = batch_layout(ns)
+        x = torch.empty(total, dtype=torch.float64, device="cuda")
+        y, w = torch.empty_like(x), torch.empty_like(x)
+        wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+        wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+        alphas = synth.uniform_pm2(seed, synth.TAG_ALPHA, len(ns))
+        px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
+        table = wx.desc_table(ns, alphas, [px + 8 * s for s in starts],
+                              [py + 8 * s for s in starts], [pw + 8 * s for s in starts])
+        dt = wx.table_to_device(table)
+        plan = wx.wxpy_batch_plan_create(table)
+        for _ in range(args.reps):
+            plan.launch(dt)
+        torch.cuda.synchronize()
+        print(json.dumps({"vecop": "batch", "segments": n, "elements": int(sum(ns)),
+                          "reps": args.reps}), flush=True)
+        return 0
     nvec = {"axpbypcz": 3, "axpby": 2, "maxpy4": 5, "maxpy8": 9, "pointwise_mult": 3,
             "norm2": 3, "dot": 4, "serve": 1}[args.vecop]
     v = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(nvec)]
