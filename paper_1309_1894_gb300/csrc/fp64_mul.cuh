@@ -75,6 +75,41 @@ __device__ __forceinline__ uint64_t mul_rn_core(const MulCoef &c, uint64_t ub, b
     return (((uint64_t)hw << 32) | m0l) + inc;
 }
 
+// RN(a * a): the same method with both operands one value, so the split is
+// taken once and the two cross products are one, doubled: P = A1^2 2^64 +
+// 2 A1 A0 2^32 + A0^2 for the limbs A1 (21 bits, hidden bit included) and A0
+// (32 bits).  The sign is always clear; the biased exponent is
+// 2 ea - 1023 + t.  `slow` as in mul_rn_core.
+__device__ __forceinline__ uint64_t sqr_rn_core(uint64_t ua, bool &slow) {
+    const uint32_t ah = (uint32_t)(ua >> 32), a0 = (uint32_t)ua;
+    const uint32_t ea = (ah >> 20) & 0x7FFu;
+    const uint32_t a1 = (ah & 0xFFFFFu) | 0x100000u;
+    const uint64_t p00 = (uint64_t)a0 * a0;
+    const uint64_t x = (uint64_t)a1 * a0;                    // < 2^53
+    const uint64_t m1 = (x << 1) + (p00 >> 32);              // < 2^54 + 2^32
+    const uint64_t top = (uint64_t)a1 * a1 + (m1 >> 32);     // P >> 64, < 2^42
+    const uint32_t w0 = (uint32_t)p00, w1 = (uint32_t)m1;
+    const uint32_t tl = (uint32_t)top, th = (uint32_t)(top >> 32);
+    const uint32_t t = th >> 9;
+    const uint32_t sh = 20 + t;
+    const uint32_t m0l = __funnelshift_r(w1, tl, sh);
+    const uint32_t m0h = __funnelshift_r(tl, th, sh);
+    const uint32_t rnd = (w1 >> (sh - 1)) & 1u;
+    const uint32_t stk = (w0 | (w1 << (33 - sh))) != 0u;
+    const uint32_t inc = rnd & (stk | m0l);
+    const int32_t ebase = 2 * (int32_t)ea - 1024 + (int32_t)t;  // result exponent - 1
+    slow = slow || (ea - 1u >= 0x7FEu) || ((uint32_t)ebase >= 0x7FDu);
+    const uint32_t hw = ((uint32_t)ebase << 20) + m0h;
+    return (((uint64_t)hw << 32) | m0l) + inc;
+}
+
+__device__ __forceinline__ uint64_t sqr_rn_bits(uint64_t ua) {
+    bool slow = false;
+    uint64_t bits = sqr_rn_core(ua, slow);
+    if (slow) bits = mul_rn_hw_bits(ua, ua);
+    return bits;
+}
+
 // RN(a * b) on two bit patterns, the hardware instruction out of line for the
 // cases the fast path leaves out.
 __device__ __forceinline__ uint64_t mul_rn_bits(uint64_t ua, uint64_t ub) {

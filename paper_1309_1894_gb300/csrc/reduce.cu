@@ -118,7 +118,7 @@ __device__ __forceinline__ void element(const ReduceArgs &a, double x, double y,
         if (slow) pb = mul_rn_hw_bits(bits_of(a.alpha), bits_of(x));  // out of line
         w = __dadd_rn(double_of(pb), y);
         const uint64_t wb = opaque_bits(w);
-        const uint64_t tb = mul_rn_bits(wb, KIND == 0 ? wb : bits_of(z));
+        const uint64_t tb = KIND == 0 ? sqr_rn_bits(wb) : mul_rn_bits(wb, bits_of(z));
         t = double_of(tb);
     } else {
         w = __dadd_rn(__dmul_rn(a.alpha, x), y);

@@ -302,3 +302,42 @@ def test_configuration_search(tmp_path):
                                                            r["sum_levels"])
     finally:
         wx.wxpy_tune_clear()
+
+
+def test_squares_one_per_tile():
+    """Each term of norm2 exactly: a full tile holding one nonzero element v
+    (x = v, y = 0, alpha = 1, so w = v) and zeros sums to that term, RN(v*v).
+    The tile sums are read from the caller-owned workspace (a 256-byte header,
+    then one double per tile): the cross-tile tree works in place on its lower
+    half, so the values sit in the upper half of a power-of-two tile count.
+    Values aim at the integer square's branches: exact squares and ties, the
+    sqrt(2) boundary where the product gains a bit, the edges of overflow and
+    underflow, specials."""
+    rng = np.random.default_rng(11)
+    vals = list(np.ldexp(1 + rng.integers(0, 1 << 52, 1200) * 2.0 ** -52,
+                         rng.integers(-520, 520, 1200)) * rng.choice([-1.0, 1.0], 1200))
+    k = np.arange(1, 170, dtype=np.float64)
+    vals += list((k * 2 ** 13 + 1) * 2.0 ** -30)                       # 27-bit: exact squares
+    vals += list((k * 2 ** 13 + 0.5) * 2.0 ** -30)                     # 28-bit: ties
+    vals += list(np.sqrt(2.0) * (1 + k * 2.0 ** -52))
+    vals += list(np.nextafter(np.sqrt(2.0), 0) * (1 - k * 2.0 ** -52))
+    vals += [1.3407807929942596e154, np.nextafter(1.3407807929942596e154, 0), 1.4916681462400413e-154,
+             2.0 ** -511, 2.0 ** -512, 2.0 ** 511, 2.0 ** 512, 5e-324, -0.0, np.inf, np.nan, 1.0]
+    vals = np.array(vals, dtype=np.float64)
+    tiles = 1 << int(np.ceil(np.log2(2 * len(vals))))
+    first = tiles // 2
+    n = T * tiles
+    xh = np.zeros(n)
+    xh[(first + np.arange(len(vals))) * T + 4099] = vals
+    x = torch.from_numpy(xh).cuda()
+    y = torch.zeros_like(x)
+    with np.errstate(over="ignore", invalid="ignore"):
+        want = vals * vals
+    for mul in (0, 16):
+        wx.wxpy_reduce_pipes(mul)
+        ws = wx.reduce_workspace(n)
+        wx.wxpy_norm2(1.0, x, y, workspace=ws)
+        torch.cuda.synchronize()
+        sums = ws[256 + 8 * first: 256 + 8 * (first + len(vals))].cpu().numpy().view(np.float64)
+        ok = (sums.view(np.uint64) == want.view(np.uint64)) | (np.isnan(sums) & np.isnan(want))
+        assert ok.all(), (mul, vals[~ok][:5], sums[~ok][:5], want[~ok][:5])
