@@ -255,14 +255,15 @@ __device__ __forceinline__ void finish_grid(const ReduceArgs &a, bool &last) {
 }
 
 // Register-loaded path: four resident blocks (64 registers), measured 4-5 %
-// faster than three.  VEC: full tiles by 32-byte vectors (co-aligned
-// pointers); the last tile, and every tile otherwise, element by element.
+// faster than three.  VEC: full tiles by 32-byte vectors (32-byte aligned
+// pointers), else element by element; the last, ragged tile always element by
+// element with FP64 products.  The product split applies to every full tile.
 template <int KIND, bool VEC, int SUML = 0>
 __global__ void __launch_bounds__(kThreads, 4) wxpy_reduce_kernel(const ReduceArgs a) {
     __shared__ double red[kThreads][4];
     __shared__ bool last;
-    const int64_t full = VEC ? a.n / kTile : 0;  // tiles with every element present
-    unsigned slot = (blockIdx.x * 7u) & 15u;    // block-uniform rotation of the pipe choice
+    const int64_t full = a.n / kTile;        // tiles with every element present
+    unsigned slot = (blockIdx.x * 7u) & 15u;  // block-uniform rotation of the pipe choice
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         double s;
         if (tile >= full) s = tile_sum<KIND, false, false>(a, tile, red);

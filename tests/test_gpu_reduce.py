@@ -135,7 +135,8 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
 @pytest.mark.parametrize("mul", [0, 16])
 @pytest.mark.parametrize("suml", [0, 3])
-def test_special_and_wide_values(kind, mul, suml):
+@pytest.mark.parametrize("offs", [(0, 0, 0, 0), (8, 8, 8, 8)])
+def test_special_and_wide_values(kind, mul, suml, offs):
     wx.wxpy_reduce_pipes(mul)
     wx.wxpy_reduce_sum_levels(suml)
     sv = np.array(pins.special_values())
@@ -145,9 +146,9 @@ def test_special_and_wide_values(kind, mul, suml):
         y = np.resize(np.tile(sv, len(sv)), n)
         z = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-300, 300, n))
         for alpha in (1.0, -0.75, 2.0 ** -600):
-            w_got, r_got = run(kind, alpha, x, y, z, (0, 0, 0, 0))
+            w_got, r_got = run(kind, alpha, x, y, z, offs)
             w_want, r_want = want(kind, alpha, x, y, z)
-            assert same_vec(w_got, w_want) and same_scalar(r_got, r_want), (kind, alpha, n)
+            assert same_vec(w_got, w_want) and same_scalar(r_got, r_want), (kind, alpha, n, offs)
         # finite wide-exponent data: every branch of the integer product
         x = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-500, 500, n))
         y = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-500, 500, n))
