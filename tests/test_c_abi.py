@@ -8,7 +8,6 @@ import numpy as np
 import pytest
 
 import oracle
-import paper_1309_1894_gb300 as wx
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -17,7 +16,9 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 
 @pytest.fixture(scope="module")
 def program(tmp_path_factory):
-    wx.lib()  # the library must exist (built by __graft_entry__.build())
+    from paper_1309_1894_gb300 import build as wbuild
+    if not os.path.exists(wbuild.LIBRARY):
+        wbuild.build()
     pkg = os.path.join(ROOT, "paper_1309_1894_gb300")
     exe = str(tmp_path_factory.mktemp("cabi") / "c_abi_example")
     subprocess.run(["gcc", "-std=c99", "-O2", "-Wall", "-Wextra", "-Werror",
