@@ -2,20 +2,27 @@
 """Benchmark of the GB300 VecWXPY library: FP64 w = alpha*x + y.
 
 Timed step: one pass of the size sweep through the C ABI ``wxpy()`` call,
-n = 2^k and 2^k + 3 for k = 10..28 (38 calls), start offsets 0/8/24 bytes by k,
-distinct x, y, w, inputs resident in HBM.  ``value`` is the algorithmic bytes
-(24 per element: read x, read y, write w) of all timed steps over their device
+n = 2^k and 2^k + 3 for k = 10..28 (38 calls), inputs resident in HBM.  The
+start offset (the same on x, y and w) cycles 0/8/24 bytes with k, and the
+alias class cycles distinct / w == x / w == y, so every (offset, alias) pair
+of the sweep is timed.  ``value`` is the algorithmic bytes (24 per element:
+read x, read y, write w -- in place too) of all timed steps over their device
 time, in GB/s.  Each step streams 12.9 GB, far more than the 129 MB L2, so the
 data of one step is gone from L2 when the next step reads it.
 
-Extra measurements in the same JSON line (not in the timed region): GB/s per n
-with the L2 flushed between repetitions and L2-resident; the host-buffer
-end-to-end number (``e2e``); the oracle on the host cores (``cpu_baseline``);
-the clocks sampled during the timed region; and, once built, the batched,
-served and stream-split workloads.
+Output.  stdout gets ONE compact JSON line (a few KB at most): the contract's
+keys (metric, value, roofline, cpu_baseline, e2e, clocks, gpu_launches, ...)
+and a short summary of every other measured leg.  The full record of those
+legs -- GB/s per n L2-flushed and L2-resident, the alias and mixed-offset rows,
+the tuner's buckets, the stream split at n = 2^30, the batched and served
+workloads, the sibling kernels, the fused reductions and the host family --
+goes to the ``--extras`` file (one JSON object), and ``--jsonl`` appends one
+row per measured case.
 
-``--impl reference`` times the CPU oracle, as it stands, on a bounded sample of
-the same sweep and prints the same metric with "impl": "reference".
+``--impl reference`` times the CPU oracle, as it stands, on the named CPU
+sample of the same sweep (the calls with n <= 2^24 + 3), the sample the repo
+arm's ``cpu_baseline`` times as well, and prints the same metric with
+"impl": "reference".
 
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent
 replica of the step on its own GPU (the operation has no exchange step), the
@@ -43,18 +50,48 @@ UNIT = "GB/s"
 BYTES_PER_ELEM = 24
 SWEEP_K = range(10, 29)
 OFFSETS = (0, 8, 24)
+ALIASES = ("distinct", "w=x", "w=y")
 DOMINANT_K = 28
-WORKLOAD = ("size sweep of single-call FP64 w = alpha*x + y: n = 2^k and 2^k+3 for "
-            "k = 10..28, start offsets 0/8/24 B by k, distinct x, y, w, 38 calls per step")
+WORKLOAD = ("FP64 wxpy size sweep: n = 2^k, 2^k+3, k = 10..28, offsets 0/8/24 B, "
+            "alias distinct/w=x/w=y, 38 calls per step")
+# The CPU sample both arms time: the sweep's calls with n <= 2^24 + 3.
+CPU_SAMPLE_K = 24
+CPU_SAMPLE = ("one pass = the sweep's 30 calls with k = 10..24 (n = 2^k and 2^k+3, same "
+              "offsets and alias classes, 1.61 GB of algorithmic bytes), CPU oracle")
+# A log tail of about 1500 characters must hold the whole stdout line.
+HEADLINE_MAX_BYTES = 1400
+CPU_SAMPLE_SHORT = f"n <= 2^{CPU_SAMPLE_K}+3 calls of the sweep"
+EXTRAS_DEFAULT = os.path.join("bench_out", "extras.json")
 
 
-def sweep_calls():
-    """(n, element offset) of the 38 calls of one step."""
+def sweep_calls(max_k: int = SWEEP_K[-1]):
+    """(n, element offset, alias class) of the calls of one step, k <= max_k.
+
+    The offset cycles with k % 3; the alias class with k // 3 for the 2^k call
+    and k // 3 + 1 for the 2^k + 3 call, so that all nine (offset, alias)
+    pairs occur."""
     calls = []
     for k in SWEEP_K:
-        for d in (0, 3):
-            calls.append(((1 << k) + d, OFFSETS[k % 3] // 8))
+        if k > max_k:
+            break
+        for j, d in enumerate((0, 3)):
+            calls.append(((1 << k) + d, OFFSETS[k % 3] // 8, ALIASES[(k // 3 + j) % 3]))
     return calls
+
+
+def call_pointers(px, py, pw, n, o, alias):
+    """Addresses (x, y, w) of a sweep call on buffers at px, py, pw: w is x or
+    y itself for the in-place classes."""
+    a, b = px + 8 * o, py + 8 * o
+    c = a if alias == "w=x" else (b if alias == "w=y" else pw + 8 * o)
+    return a, b, c
+
+
+def call_alpha(alpha, alias):
+    """alpha of a sweep call: the w = x calls use alpha / 2 (|alpha / 2| < 1),
+    so that x, updated in place once per step, stays bounded however many
+    steps run; the other classes use alpha."""
+    return alpha * 0.5 if alias == "w=x" else alpha
 
 
 # ----------------------------------------------------------------- helpers
@@ -195,46 +232,81 @@ def sum_over_ranks(dist, value: float) -> float:
 
 
 # ----------------------------------------------------------------- CPU oracle legs
-def cpu_oracle_rate(max_k: int, seconds: float, threads: int = 1):
-    """GB/s of the oracle over passes of the sweep restricted to k <= max_k,
-    repeated for about ``seconds``; ``threads`` > 1 splits each call into
-    contiguous chunks run by a thread pool (the oracle function unchanged)."""
-    import numpy as np
-    import oracle
-    from paper_1309_1894_gb300 import synth
-    from concurrent.futures import ThreadPoolExecutor
+class CpuSample:
+    """The named CPU sample of the sweep (CPU_SAMPLE): the calls with
+    k <= CPU_SAMPLE_K on host vectors from the same seeded generator, run
+    through the oracle unchanged.  ``threads`` > 1 splits each call into
+    contiguous chunks run by a thread pool (the same oracle function on each
+    chunk)."""
 
-    nmax = (1 << max_k) + 3
-    alpha, xh, yh = synth.vectors(synth.BASE_SEED, nmax + 3)
-    wh = np.empty_like(xh)
-    calls = [(n, o) for (n, o) in sweep_calls() if n <= nmax]
-    pool = ThreadPoolExecutor(threads) if threads > 1 else None
+    def __init__(self, threads: int = 1):
+        import numpy as np
+        from paper_1309_1894_gb300 import synth
+        self.calls = sweep_calls(CPU_SAMPLE_K)
+        nmax = max(n for n, _, _ in self.calls)
+        alpha, self.x, self.y = synth.vectors(synth.BASE_SEED, nmax + 3)
+        self.alpha = float(alpha)
+        self.w = np.empty_like(self.x)
+        self.bytes_per_pass = sum(BYTES_PER_ELEM * n for n, _, _ in self.calls)
+        self.threads = threads
+        self.pool = None
+        if threads > 1:
+            from concurrent.futures import ThreadPoolExecutor
+            self.pool = ThreadPoolExecutor(threads)
 
-    def one(n, o):
-        if pool is None:
-            oracle.wxpy_into(alpha, xh[o:o + n], yh[o:o + n], wh[o:o + n])
+    def _one(self, n, o, alias):
+        import oracle
+        x, y = self.x[o:o + n], self.y[o:o + n]
+        w = x if alias == "w=x" else (y if alias == "w=y" else self.w[o:o + n])
+        al = call_alpha(self.alpha, alias)
+        if self.pool is None:
+            oracle.wxpy_into(al, x, y, w)
             return
-        bounds = [o + (n * t) // threads for t in range(threads + 1)]
-        futs = [pool.submit(oracle.wxpy_into, alpha, xh[a:b], yh[a:b], wh[a:b])
-                for a, b in zip(bounds[:-1], bounds[1:])]
+        t = self.threads
+        bounds = [(n * i) // t for i in range(t + 1)]
+        futs = [self.pool.submit(oracle.wxpy_into, al, x[p:q], y[p:q], w[p:q])
+                for p, q in zip(bounds[:-1], bounds[1:])]
         for f in futs:
             f.result()
 
-    for (n, o) in calls:  # warm-up pass
-        one(n, o)
-    passes, byts = 0, 0
-    t0 = time.perf_counter()
-    while True:
-        for (n, o) in calls:
-            one(n, o)
-            byts += BYTES_PER_ELEM * n
-        passes += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    if pool is not None:
-        pool.shutdown()
-    return byts / dt / 1e9, passes, dt
+    def one_pass(self):
+        for c in self.calls:
+            self._one(*c)
+
+    def timed(self, passes: int = 0, seconds: float = 0.0):
+        """(GB/s, passes, seconds) over ``passes`` passes, or as many passes
+        as fit in ``seconds`` (at least one)."""
+        done = 0
+        t0 = time.perf_counter()
+        while True:
+            self.one_pass()
+            done += 1
+            dt = time.perf_counter() - t0
+            if (passes and done >= passes) or (not passes and dt >= seconds):
+                break
+        return self.bytes_per_pass * done / dt / 1e9, done, dt
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+
+
+def cpu_baseline_leg(seconds: float):
+    """The repo arm's cpu_baseline: the CPU sample single-threaded for about
+    ``seconds``, then on all host cores for a third of that."""
+    one = CpuSample(1)
+    one.one_pass()  # warm-up pass: first touch of the host pages
+    rate1, passes, dt = one.timed(seconds=seconds)
+    one.close()
+    cores = host_cores()
+    allc = CpuSample(cores)
+    allc.one_pass()
+    rate_all, passes_all, _ = allc.timed(seconds=max(2.0, seconds / 3))
+    allc.close()
+    return {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE}; {passes} passes in {dt:.1f} s, one thread",
+            "all_cores": {"value": rate_all, "cores": cores, "passes": passes_all,
+                          "how": "each call split into contiguous chunks, one thread each"}}
 
 
 def host_cores() -> int:
@@ -246,40 +318,25 @@ def host_cores() -> int:
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle on the host cores: each step is one pass of the CPU sample
+    (CPU_SAMPLE), the same sample the repo arm's cpu_baseline times."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np
-    import oracle
-    from paper_1309_1894_gb300 import synth
-    max_k = 20  # bounded sample: k = 10..20 per step
-    nmax = (1 << max_k) + 3
-    alpha, xh, yh = synth.vectors(synth.BASE_SEED, nmax + 3)
-    wh = np.empty_like(xh)
-    calls = [(n, o) for (n, o) in sweep_calls() if n <= nmax]
-    step_bytes = sum(BYTES_PER_ELEM * n for n, _ in calls)
-
-    def step():
-        for (n, o) in calls:
-            oracle.wxpy_into(alpha, xh[o:o + n], yh[o:o + n], wh[o:o + n])
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = step_bytes * args.steps / dt / 1e9
-    sample = (f"each step: the sweep's calls with k = 10..{max_k} (22 calls, "
-              f"{step_bytes / 1e6:.1f} MB), CPU oracle, single thread")
+    smp = CpuSample(1)
+    for _ in range(max(args.warmup, 1)):
+        smp.one_pass()
+    value, passes, dt = smp.timed(passes=args.steps)
+    smp.close()
+    sample = f"{CPU_SAMPLE_SHORT}, one pass per step, one thread"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "ms_per_step": dt / passes * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": {"workload": WORKLOAD, "cpu_sample": CPU_SAMPLE_SHORT},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "passes": passes},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -289,6 +346,25 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def lookup_ptr(wx, n, a, b, c):
+    """(variant, source) that wxpy(n, ., a, b, c) runs; source 0 default, 1 tuned, 2 forced."""
+    import ctypes
+    info = wx.binding.VariantInfo()
+    src = ctypes.c_int()
+    wx.check(wx.lib().wxpy_lookup(n, a, b, c, ctypes.byref(info), ctypes.byref(src)),
+             "wxpy_lookup")
+    return info.as_dict(), src.value
+
+
+def split_count(v, n):
+    """Launches of one wxpy() call: the variant's streams, halved while a
+    piece would be under 65536 elements (the rule of the stream split)."""
+    s = v["streams"]
+    while s > 1 and n // s < 65536:
+        s //= 2
+    return s
+
+
 def run_ours(args):
     import torch
     import paper_1309_1894_gb300 as wx
@@ -303,7 +379,7 @@ def run_ours(args):
     sh = stream.cuda_stream or None
 
     calls = sweep_calls()
-    nmax = max(n for n, _ in calls)
+    nmax = max(n for n, _, _ in calls)
     x = torch.empty(nmax + 8, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     w = torch.empty_like(x)
@@ -312,34 +388,32 @@ def run_ours(args):
     wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
     alpha = synth.alpha_scalar(seed)
     px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
-    cargs = [(n, px + 8 * o, py + 8 * o, pw + 8 * o) for (n, o) in calls]
-    step_bytes = sum(BYTES_PER_ELEM * n for n, _ in calls)
+    cargs = [(n, call_alpha(alpha, al), *call_pointers(px, py, pw, n, o, al))
+             for (n, o, al) in calls]
+    step_bytes = sum(BYTES_PER_ELEM * n for n, _, _ in calls)
 
-    # The method: one empirical search per size bucket of the sweep (or the
-    # cells of a saved tune cache), before anything is timed.
+    # The method: one empirical search per size bucket of the sweep and per
+    # alias group it times (or the cells of a saved tune cache), before
+    # anything is timed.
     tuning = tune_buckets(wx, args, torch)
 
-    # launches per call: the variant wxpy() runs, after the stream-split rule
     launches_per_step = 0
-    variants = {}
-    for (n, o) in calls:
-        v, src = wx.wxpy_lookup(x[o:o + n], y[o:o + n], w[o:o + n])
-        s = v["streams"]
-        while s > 1 and n // s < 65536:
-            s //= 2
-        launches_per_step += s
-        variants[n] = (v, src)
-    dom = [i for i, (n, _) in enumerate(calls) if n >= (1 << DOMINANT_K)]
+    variants = []
+    for (n, al, a, b, c) in cargs:
+        v, src = lookup_ptr(wx, n, a, b, c)
+        launches_per_step += split_count(v, n)
+        variants.append((v, src))
+    dom = [i for i, (n, _, _) in enumerate(calls) if n >= (1 << DOMINANT_K)]
 
     def step(ev_pairs=None):
-        for i, (n, a, b, c) in enumerate(cargs):
+        for i, ca in enumerate(cargs):
             if ev_pairs is not None and i in dom:
                 e0, e1 = ev_pairs.pop()
                 e0.record(stream)
-                rc = lib.wxpy(n, alpha, a, b, c, sh)
+                rc = lib.wxpy(*ca, sh)
                 e1.record(stream)
             else:
-                rc = lib.wxpy(n, alpha, a, b, c, sh)
+                rc = lib.wxpy(*ca, sh)
             if rc != 0:
                 wx.check(rc, "wxpy")
 
@@ -371,6 +445,7 @@ def run_ours(args):
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     peak, peak_src = load_peaks()
     traffic = profiled_traffic()
+    vdom, sdom = variants[dom[0]]
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -380,27 +455,31 @@ def run_ours(args):
                    "l2": "inputs larger than L2: each step streams "
                          f"{step_bytes / 1e9:.1f} GB against a 129 MB L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "variant_n_2e28": variants[1 << DOMINANT_K][0],
-                   "variant_source": {0: "default", 1: "tuned", 2: "forced"}[
-                       variants[1 << DOMINANT_K][1]]},
+                   "cpu_sample": CPU_SAMPLE,
+                   "variant_n_2e28": vdom["id"],
+                   "variant_source": {0: "default", 1: "tuned", 2: "forced"}[sdom]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "wxpy_single_kernel (n = 2^28 and 2^28+3 launches)",
+                     "kernel": "wxpy_single_kernel, the n = 2^28 and 2^28+3 launches",
                      "peak_source": f"{peak_src} hbm_gbs",
                      "frac_of_nominal_8TBs": achieved / 8000.0},
         "gpu_launches": launches_per_step * K,
         "tuning": tuning,
+        "variants": [{"n": n, "offset_bytes": 8 * o, "alias": al, "variant": v["id"],
+                      "source": s, "launches": split_count(v, n)}
+                     for (n, o, al), (v, s) in zip(calls, variants)],
     }
     result["clocks"] = clocks.summary()
 
     if rank == 0 and not args.no_extras:
         result["sweep"] = measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak)
         result["fp64_offload"] = measure_offload(wx, lib, torch, x, y, w, alpha, sh, stream,
-                                                 peak, variants[1 << DOMINANT_K][0])
+                                                 peak, vdom)
     result["e2e"] = measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist)
     del x, y, w
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_extras:
+        result["config1"] = measure_config1(wx, lib, torch, dev, sh, stream, peak)
         result["streams"] = measure_streams(wx, lib, torch, dev, sh, stream, peak)
         result["batched"] = measure_batched(wx, lib, torch, dev, sh, stream, peak)
         result["vecops"] = measure_vecops(wx, torch, dev, stream, peak)
@@ -409,21 +488,99 @@ def run_ours(args):
             result["served"] = measure_served(args.serve_seconds)
         result["cpu_family"] = measure_cpu_family()
     if rank == 0:
-        rate1, passes, dt = cpu_oracle_rate(24, args.cpu_seconds, threads=1)
-        cores = host_cores()
-        rate_all, _, _ = cpu_oracle_rate(24, max(2.0, args.cpu_seconds / 3), threads=cores)
-        result["cpu_baseline"] = {
-            "value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{passes} passes over the sweep's calls with k = 10..24 "
-                      f"(30 calls, {dt:.1f} s), single thread",
-            "all_cores": {"value": rate_all, "cores": cores,
-                          "how": "each call split into contiguous chunks, one thread each"}}
-        print(json.dumps(result), flush=True)
+        result["cpu_baseline"] = cpu_baseline_leg(args.cpu_seconds)
+        if args.extras:
+            d = os.path.dirname(args.extras)
+            if d:
+                os.makedirs(d, exist_ok=True)
+            with open(args.extras, "w") as f:
+                json.dump(result, f, indent=1)
+            result["extras_file"] = args.extras
         if args.jsonl:
             write_jsonl(args.jsonl, result)
+        print(json.dumps(headline(result)), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _r(v, digits=4):
+    """A number rounded to ``digits`` significant digits (None stays None)."""
+    if v is None or isinstance(v, bool) or not isinstance(v, (int, float)):
+        return v
+    if v == 0 or not math.isfinite(v):
+        return v
+    return float(f"{v:.{digits}g}")
+
+
+def _pick(d, keys, digits=4):
+    return {k: _r(d[k], digits) for k in keys if k in d}
+
+
+def headline(result):
+    """The one stdout line: the contract's keys, and a few numbers of the
+    other legs; everything else stays in the extras file.  Kept under
+    HEADLINE_MAX_BYTES so that a log tail of the run holds it whole."""
+    line = {k: result[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup",
+                                   "ms_per_step", "higher_is_better", "scaling",
+                                   "vs_baseline", "dtype", "data") if k in result}
+    line["value"] = _r(line.get("value"), 6)
+    line["ms_per_step"] = _r(line.get("ms_per_step"), 5)
+    cfg = result.get("config", {})
+    line["config"] = {k: cfg[k] for k in ("workload", "parallelism", "variant_n_2e28")
+                      if k in cfg}
+    if "step_bytes" in cfg:
+        line["config"]["l2"] = f"no flush: {cfg['step_bytes'] / 1e9:.1f} GB/step > L2"
+    line["config"]["cpu_sample"] = CPU_SAMPLE_SHORT
+    rf = result.get("roofline")
+    if rf:
+        line["roofline"] = {"bound": rf["bound"], "achieved": _r(rf["achieved"]),
+                            "peak": rf["peak"], "unit": rf["unit"], "frac": _r(rf["frac"]),
+                            "traffic": _r(rf["traffic"]), "kernel": "n=2^28(+3) launches"}
+    cb = result.get("cpu_baseline")
+    if cb:
+        line["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
+                                "kind": cb["kind"], "sample": line["config"]["cpu_sample"],
+                                "all_cores": _r(cb.get("all_cores", {}).get("value")),
+                                "host_cores": cb.get("all_cores", {}).get("cores")}
+    e = result.get("e2e")
+    if e:
+        line["e2e"] = {"value": _r(e["value"]), "unit": e["unit"],
+                       "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+    if "clocks" in result:
+        c = result["clocks"]
+        line["clocks"] = {"sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"),
+                          "reasons": c.get("reasons", [])}
+    line["gpu_launches"] = result.get("gpu_launches")
+    legs = {}
+    c1 = result.get("config1")
+    if c1:  # GB/s of n = 2^20: L2 flushed, L2 resident
+        legs["n2e20_gbs"] = [_r(c1.get("gbs_l2_flushed"), 4), _r(c1.get("gbs_l2_resident"), 4)]
+    sw = result.get("sweep")
+    if isinstance(sw, dict):
+        big = [r for r in sw.get("rows", []) if r["n"] >= (1 << 24) and "case" not in r]
+        if big:
+            legs["min_frac_n_ge_2e24"] = _r(min(r["frac_of_peak_flushed"] for r in big), 3)
+        mixed = [r["frac_of_peak_flushed"] for r in sw.get("rows", [])
+                 if r["n"] == (1 << DOMINANT_K) and r.get("case", "").startswith("mixed")]
+        if mixed:
+            legs["mixed_frac_2e28"] = _r(min(mixed), 3)
+    bt = result.get("batched")
+    if bt:  # graph-replayed batch GB/s, speedup over per-call launches
+        legs["batch_gbs_x"] = [_r(bt["graph_replay"]["gbs"], 4),
+                               _r(bt["speedup_graph_vs_per_call"], 3)]
+    sv = result.get("served")
+    if sv:  # p99 ms at each rate, batched then serial
+        for mode, key in (("batched", "p99_ms_batched"), ("serial", "p99_ms_serial")):
+            legs[key] = [_r(r["p99_ms"], 3) for r in sv.get(mode, [])]
+    rd = result.get("reduce")
+    if rd:
+        legs["norm2_dot_frac"] = [_r(rd["norm2"]["frac_of_peak"], 3),
+                                  _r(rd["dot"]["frac_of_peak"], 3)]
+    if legs:
+        line["legs"] = legs
+    return line
 
 
 def case_rows(obj, path, common):
@@ -463,8 +620,9 @@ def write_jsonl(path, result):
 
 
 def tune_buckets(wx, args, torch):
-    """Run wxpy_tune for every bucket of the sweep (n = 2^k), or load the cells
-    from --tune-cache when that file exists; returns a summary."""
+    """Run wxpy_tune for every bucket of the sweep (n = 2^k) and both alias
+    groups the step times (distinct, and in place: w = x or w = y), or load
+    the cells from --tune-cache when that file exists; returns a summary."""
     t0 = time.perf_counter()
     if args.tune_cache and os.path.exists(args.tune_cache):
         wx.wxpy_tune_cache_load(args.tune_cache, check_device=True)
@@ -474,16 +632,17 @@ def tune_buckets(wx, args, torch):
         return {"source": "built-in default variant (tuning skipped)"}
     rows = []
     for k in SWEEP_K:
-        r = wx.wxpy_tune(1 << k, 0)
-        rows.append({"k": k, "variant": r["best"], "us": r["best_us"],
-                     "default_us": r["default_us"], "reference_us": r["reference_us"],
-                     "gbs": r["best_gbs"], "candidates": r["candidates"],
-                     "rejected": r["rejected"]})
+        for group, flags in (("distinct", 0), ("in_place", wx.binding.TUNE_WALIAS)):
+            r = wx.wxpy_tune(1 << k, flags)
+            rows.append({"k": k, "group": group, "variant": r["best"], "us": r["best_us"],
+                         "default_us": r["default_us"], "reference_us": r["reference_us"],
+                         "gbs": r["best_gbs"], "candidates": r["candidates"],
+                         "rejected": r["rejected"], "launch_bound": r.get("launch_bound")})
     torch.cuda.synchronize()
     if args.tune_cache:
         wx.wxpy_tune_cache_save(args.tune_cache)
-    return {"source": "wxpy_tune per bucket (L2 flushed, median timing, bitwise check "
-                      "against the reference variant)",
+    return {"source": "wxpy_tune per bucket and alias group (L2 flushed, median timing, "
+                      "bitwise check against the reference variant)",
             "seconds": time.perf_counter() - t0, "buckets": rows}
 
 
@@ -496,55 +655,157 @@ def flushed_batch(n):
     return 1 if est_us >= 200.0 else int(min(64, math.ceil(200.0 / est_us)))
 
 
+def time_flushed(lib, torch, stream, flush, batch, reps):
+    """Median per-call ms of ``batch`` (a list of wxpy argument tuples) run
+    back to back after an L2 flush, over ``reps`` runs; a device sleep is
+    queued ahead of each timed run so that the host's launch latency is not
+    part of the device time."""
+    tf = []
+    for _ in range(reps):
+        flush.sum()
+        torch.cuda._sleep(100000 + 30000 * len(batch))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for a in batch:
+            lib.wxpy(*a)
+        e1.record(stream)
+        e1.synchronize()
+        tf.append(e0.elapsed_time(e1) / len(batch))
+    return statistics.median(tf)
+
+
+def time_resident(lib, torch, stream, args, r=50):
+    """Per-call ms of ``r`` back-to-back calls on the same (L2-resident) data."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lib.wxpy(*args)
+    torch.cuda._sleep(2000000)
+    e0.record(stream)
+    for _ in range(r):
+        lib.wxpy(*args)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / r
+
+
+# Extra classes of the sweep table at n = 2^24, 2^26, 2^28: (name, x, y, w
+# start offsets in bytes, alias); "mixed a/b/c" has x, y, w at a, b, c bytes
+# past a 256-byte boundary.  x=y moves 16 bytes per element.
+CLASS_CASES = (("distinct", 0, 0, 0, "distinct"), ("w=x", 0, 0, 0, "w=x"),
+               ("w=y", 0, 0, 0, "w=y"), ("x=y", 0, 0, 0, "x=y"),
+               ("mixed 0/8/24", 0, 8, 24, "distinct"),
+               ("mixed 8/24/0", 8, 24, 0, "distinct"),
+               ("mixed 16/0/8", 16, 0, 8, "distinct"))
+
+
 def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=9):
-    """GB/s per n: median of ``reps`` with the L2 flushed (read of a 512 MB buffer)
-    before each timed run -- one call, or a batch of calls on disjoint slices for
-    short calls (flushed_batch) -- and L2-resident (back-to-back) for n <= 2^22.
-    A device sleep is queued ahead of each timed run so that the host's launch
-    latency is not part of the device time."""
+    """GB/s per call of the step, median of ``reps`` with the L2 flushed (read
+    of a 512 MB buffer) before each timed run -- one call, or a batch of calls
+    on disjoint slices for short calls (flushed_batch) -- and L2-resident
+    (back-to-back) for n <= 2^22; then the alias and mixed-offset classes
+    (CLASS_CASES) at n = 2^24, 2^26 and 2^28."""
     flush = torch.empty(64 << 20, dtype=torch.float64, device=x.device)
     flush.fill_(1.0)
-    out = []
+    rows = []
     px, py, pw = x.data_ptr(), y.data_ptr(), w.data_ptr()
-    for (n, o) in calls:
-        args = (n, alpha, px + 8 * o, py + 8 * o, pw + 8 * o, sh)
+    for (n, o, al) in calls:
+        al_a = call_alpha(alpha, al)
         b = flushed_batch(n)
         stride = (n + 64 + 31) // 32 * 32  # elements: 256-byte steps keep the offset class
         assert b == 1 or o + (b - 1) * stride + n <= x.numel()
-        batch = [(n, alpha, px + 8 * (o + i * stride), py + 8 * (o + i * stride),
-                  pw + 8 * (o + i * stride), sh) for i in range(b)]
-        tf = []
-        for _ in range(reps):
-            flush.sum()
-            torch.cuda._sleep(100000 + 30000 * b)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for a in batch:
-                lib.wxpy(*a)
-            e1.record(stream)
-            e1.synchronize()
-            tf.append(e0.elapsed_time(e1) / b)
-        row = {"n": n, "offset_bytes": 8 * o, "calls_per_flushed_run": b,
-               "gbs_l2_flushed": BYTES_PER_ELEM * n / (statistics.median(tf) / 1e3) / 1e9,
-               "us_l2_flushed": statistics.median(tf) * 1e3}
+        batch = [(n, al_a, *call_pointers(px, py, pw, n, o + i * stride, al), sh)
+                 for i in range(b)]
+        ms = time_flushed(lib, torch, stream, flush, batch, reps)
+        row = {"n": n, "offset_bytes": 8 * o, "alias": al, "calls_per_flushed_run": b,
+               "gbs_l2_flushed": BYTES_PER_ELEM * n / (ms / 1e3) / 1e9, "us_l2_flushed": ms * 1e3}
         if n <= (1 << 22) + 3:
-            r = 50
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            lib.wxpy(*args)
-            torch.cuda._sleep(2000000)
-            e0.record(stream)
-            for _ in range(r):
-                lib.wxpy(*args)
-            e1.record(stream)
-            e1.synchronize()
-            t = e0.elapsed_time(e1) / r
+            t = time_resident(lib, torch, stream, batch[0])
             row["gbs_l2_resident"] = BYTES_PER_ELEM * n / (t / 1e3) / 1e9
         row["frac_of_peak_flushed"] = row["gbs_l2_flushed"] / peak
-        out.append(row)
+        rows.append(row)
+    for k in (24, 26, 28):
+        n = 1 << k
+        for (name, ox, oy, ow, al) in CLASS_CASES:
+            a, b, c = px + ox, py + oy, pw + ow
+            if al == "w=x":
+                c = a
+            elif al == "w=y":
+                c = b
+            elif al == "x=y":
+                b = a
+            nbytes = (16 if al == "x=y" else 24) * n
+            v, src = lookup_ptr(wx, n, a, b, c)
+            ms = time_flushed(lib, torch, stream, flush, [(n, call_alpha(alpha, al), a, b, c, sh)],
+                              reps)
+            gbs = nbytes / (ms / 1e3) / 1e9
+            rows.append({"n": n, "case": name, "alias": al, "x_offset_bytes": ox,
+                         "y_offset_bytes": oy, "w_offset_bytes": ow,
+                         "bytes_per_elem": nbytes // n, "variant": v["id"],
+                         "vec_bytes": v["vec_bytes"], "variant_source": src,
+                         "gbs_l2_flushed": gbs, "us_l2_flushed": ms * 1e3,
+                         "frac_of_peak_flushed": gbs / peak})
     del flush
-    return out
+    return {"reps": reps, "rows": rows}
+
+
+def measure_config1(wx, lib, torch, dev, sh, stream, peak, reps=15, copies=16):
+    """Config 1: n = 1,048,576, alpha ~ U(-2,2), x, y ~ U(-1,1) from seed, three
+    separate 64-byte-aligned allocations, w distinct.  L2-flushed: ``copies``
+    independent (x, y, w) sets (16 x 24 MiB, together larger than L2), the L2
+    flushed, then one call on each set back to back, per-call time = total /
+    copies; also replayed from a CUDA graph of those calls.  L2-resident:
+    back-to-back calls on one set."""
+    from paper_1309_1894_gb300 import synth
+    n = 1 << 20
+    seed = synth.BASE_SEED + 1
+    alpha = synth.alpha_scalar(seed)
+    sets = []
+    for i in range(copies):
+        xs = torch.empty(n, dtype=torch.float64, device=dev)
+        ys, wss = torch.empty_like(xs), torch.empty_like(xs)
+        wx.wxpy_fill_uniform(xs, seed, synth.TAG_X)
+        wx.wxpy_fill_uniform(ys, seed, synth.TAG_Y)
+        assert xs.data_ptr() % 64 == 0 and ys.data_ptr() % 64 == 0 and wss.data_ptr() % 64 == 0
+        sets.append((xs, ys, wss))
+    flush = torch.empty(64 << 20, dtype=torch.float64, device=dev)
+    flush.fill_(1.0)
+    batch = [(n, alpha, a.data_ptr(), b.data_ptr(), c.data_ptr(), sh) for a, b, c in sets]
+    ms_f = time_flushed(lib, torch, stream, flush, batch, reps)
+    ms_r = time_resident(lib, torch, stream, batch[0], r=200)
+    # The same calls captured into one CUDA graph (launch gaps of the graph).
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    with torch.cuda.stream(cap):
+        csh = cap.cuda_stream
+        for a in batch:  # warm the capture stream's lazily created state
+            lib.wxpy(*a[:-1], csh)
+        cap.synchronize()
+        with torch.cuda.graph(g, stream=cap):
+            for a in batch:
+                wx.check(lib.wxpy(*a[:-1], csh), "wxpy (capture)")
+    tg = []
+    for _ in range(reps):
+        flush.sum()
+        torch.cuda._sleep(1000000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        tg.append(e0.elapsed_time(e1) / copies)
+    ms_g = statistics.median(tg)
+    del g, sets, flush
+    gbs = lambda ms: BYTES_PER_ELEM * n / (ms / 1e3) / 1e9
+    v, src = lookup_ptr(wx, *batch[0][:1], *batch[0][2:5])
+    return {"n": n, "alpha": alpha, "copies": copies, "reps": reps, "variant": v["id"],
+            "variant_source": src,
+            "gbs_l2_flushed": gbs(ms_f), "us_l2_flushed": ms_f * 1e3,
+            "gbs_l2_resident": gbs(ms_r), "us_l2_resident": ms_r * 1e3,
+            "gbs_graph_flushed": gbs(ms_g), "us_graph_flushed": ms_g * 1e3,
+            "frac_of_peak_flushed": gbs(ms_f) / peak,
+            "at_peak_us": BYTES_PER_ELEM * n / (peak * 1e9) * 1e6}
 
 
 def measure_offload(wx, lib, torch, x, y, w, alpha, sh, stream, peak, tuned, reps=20):
@@ -579,20 +840,22 @@ def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
     wxpy_host(): per call the library copies x and y in, runs the tuned kernel
     and copies w out, chunk by chunk, overlapped on its internal streams, all
     inside the timed region; bytes counted from the copies."""
-    nmax = max(n for n, _ in calls)
+    nmax = max(n for n, _, _ in calls)
     steps = max(1, args.e2e_steps)
     hx = torch.empty(nmax + 8, dtype=torch.float64, pin_memory=True)
     hy = torch.empty_like(hx, pin_memory=True)
     hw = torch.empty_like(hx, pin_memory=True)
     hx.uniform_(-1, 1)
     hy.uniform_(-1, 1)
-    h2d = sum(16 * n for n, _ in calls)
-    d2h = sum(8 * n for n, _ in calls)
+    h2d = sum(16 * n for n, _, _ in calls)
+    d2h = sum(8 * n for n, _, _ in calls)
     px, py, pw = hx.data_ptr(), hy.data_ptr(), hw.data_ptr()
+    hargs = [(n, call_alpha(alpha, al), *call_pointers(px, py, pw, n, o, al), sh)
+             for (n, o, al) in calls]
 
     def step():
-        for (n, o) in calls:
-            wx.check(lib.wxpy_host(n, alpha, px + 8 * o, py + 8 * o, pw + 8 * o, sh), "wxpy_host")
+        for a in hargs:
+            wx.check(lib.wxpy_host(*a), "wxpy_host")
 
     def run(direct):
         wx.wxpy_host_config(1 << 22, 3, direct)
@@ -607,7 +870,7 @@ def measure_e2e(wx, lib, torch, dev, alpha, calls, sh, stream, args, dist):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(dist, e0.elapsed_time(e1))
-        total = sum_over_ranks(dist, sum(BYTES_PER_ELEM * n for n, _ in calls) * steps)
+        total = sum_over_ranks(dist, sum(BYTES_PER_ELEM * n for n, _, _ in calls) * steps)
         return total / (ms / 1e3) / 1e9
 
     staged = run(False)
@@ -857,16 +1120,23 @@ SERVE_BACKFILL_US = 5000
 def measure_served(seconds):
     """Poisson arrivals at five rates from 1e3 to 1e6 requests/s, n log-uniform in
     [2^8, 2^24], alpha ~ U(-2,2), a 16 GiB admission budget, each rate for
-    ``seconds``: the continuous-batching server against the same server
-    launching every request call by call (serial baseline)."""
-    from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL
+    ``seconds``: the continuous-batching server (per batch: one fill launch
+    writing the requests' x and y into their resident buffers, then one
+    segmented launch reading them and writing w), the same with backfill
+    admission, the serial baseline over the identical data path (per request:
+    fill x, fill y, one wxpy() call), and the fused option (one kernel per
+    batch generating x and y in registers; reads nothing).  elem/s counts
+    completed elements; GB/s counts wxpy's 24 bytes per element (the fill
+    writes 16 more in every mode but the fused one)."""
+    from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL, SERVE_FUSED
     from paper_1309_1894_gb300 import synth
     out = {"budget_gib": 16, "n_range": [1 << 8, 1 << 24], "seconds_per_rate": seconds,
            "rates": list(SERVE_RATES), "backfill_aging_us": SERVE_BACKFILL_US,
-           "batched": [], "batched_backfill": [], "serial": []}
+           "batched": [], "batched_backfill": [], "serial": [], "fused": []}
     for name, mode, admission in (("batched", SERVE_BATCHED, 0),
                                   ("batched_backfill", SERVE_BATCHED, SERVE_BACKFILL_US),
-                                  ("serial", SERVE_SERIAL, 0)):
+                                  ("serial", SERVE_SERIAL, 0),
+                                  ("fused", SERVE_FUSED, 0)):
         with Server(budget_bytes=16 << 30, max_slots=4096, n_streams=2, max_batch=1024,
                     max_queue=65536, mode=mode, admission_us=admission) as sv:
             for i, rate in enumerate(SERVE_RATES):
@@ -884,7 +1154,7 @@ def measure_served(seconds):
                     "gbs": r["gbs"], "completed_per_s": r["completed"] / r["wall_s"],
                     "max_queue": r["max_queue"], "backlog_at_end": r["backlog_at_end"],
                     "mean_batch": r["mean_batch"], "launches": r["launches"],
-                    "drained": bool(r["drained"])})
+                    "max_inflight": st["max_inflight"], "drained": bool(r["drained"])})
     return out
 
 
@@ -931,6 +1201,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--jsonl", default=None,
                     help="also append one JSON line per measured case to this file")
+    ap.add_argument("--extras", default=EXTRAS_DEFAULT,
+                    help="write the full record of every measured leg to this JSON file "
+                         "('' skips it); stdout gets the compact headline line only")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-n sweep and stream-split measurements")

@@ -15,6 +15,7 @@ def test_reference_arm_line():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [t for t in r.stdout.splitlines() if t.strip()]
     assert len(lines) == 1
+    assert len(lines[0].encode()) <= 1400
     d = json.loads(lines[0])
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
@@ -22,6 +23,10 @@ def test_reference_arm_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 3
     assert d["value"] > 0 and d["dtype"] == "f64" and "workload" in d["config"]
+    # the repo arm's cpu_baseline names the same sample in its config
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"]["cpu_sample"] == bench.CPU_SAMPLE_SHORT
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]

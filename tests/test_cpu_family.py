@@ -87,6 +87,7 @@ SIZES = [0, 1, 2, 3, 7, 8, 9, 31, 33, 67, 1000, 4099, 100003]
 
 
 def variants_one_thread():
+    wbuild.build_cpu()  # parametrisation runs at collection, before the fixture
     nt = cf.variant_count() // 39
     return [(f * 13 + k) * nt for f in range(3) for k in range(13)]
 
