@@ -1309,8 +1309,8 @@ def run_vecop(args):
                 for t in tickets:
                     sv.wait(t)
                     sv.release(t)
-        print(json.dumps({"vecop": "serve", "n_max": n, "requests": 64, "reps": args.reps}),
-              flush=True)
+        print(json.dumps({"vecop": "serve", "n_max": n, "requests": 64, "reps": args.reps,
+                          "elements": int(sum(int(m) for m in lens))}), flush=True)
         return 0
     if args.vecop in ("norm2", "dot"):
         ws = wx.reduce_workspace(n)

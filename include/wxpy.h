@@ -473,14 +473,19 @@ int wxpy_batch(const wxpy_desc *host_table, const wxpy_desc *dev_table, int64_t 
  * library, held by every GPU that loads the library until the process exits.
  * Limit: count <= 65536 (WXPY_EINVAL above it, before anything is launched).
  * The first call on a device looks up the scratch address
- * (cudaGetSymbolAddress) once for that device; make that first call before
- * any stream capture.  Every call shares the one scratch array, which keeps
- * the last call's contents (each call rebuilds what it reads): calls that
- * overlap on the GPU -- on different streams, or from different threads --
- * race on it and must be serialised by the caller.  Descriptors are checked on
- * the device only for n <= 0 and for null or misaligned pointers (such
- * problems are skipped); the caller guarantees that the problems are
- * independent.  Asynchronous on `stream`. */
+ * (cudaGetSymbolAddress) for that device and keeps it once the lookup has
+ * succeeded (a failed lookup returns WXPY_ECUDA and is retried by the next
+ * call); make that first call before any stream capture.  Every call shares
+ * the one scratch array, which keeps the last call's contents (each call
+ * rebuilds what it reads): calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race on it and must be serialised by
+ * the caller.  Descriptors are checked on the device only for n <= 0 and for
+ * null or misaligned pointers (such problems are skipped); none of the host
+ * checks of wxpy_batch() (no WXPY_EOVERLAP) runs here, so the caller
+ * guarantees what they would check: within each descriptor, w equals x, equals
+ * y, or overlaps neither of them (a partial overlap races silently), and no
+ * descriptor writes a range that another descriptor reads or writes.
+ * Asynchronous on `stream`. */
 int wxpy_batch_noalloc(const wxpy_desc *dev_table, int64_t count, void *stream);
 
 /* ---- the empirical search (Sec. 2) and its persisted results ------------------ */
@@ -596,12 +601,31 @@ int wxpy_batch_launch_set(int blocks_per_sm, int fp64_offload);
 /* ---- serving: continuous batching of wxpy requests --------------------------- */
 
 /* The paper has no serving layer; this runs the operation of Sec. 3 / Fig. 1
- * for a stream of independent requests.  Each request (n, alpha, seed) gets
- * inputs x, y = U(-1,1) streams (seed, WXPY_TAG_X) and (seed, WXPY_TAG_Y) of
- * the seeded generator (wxpy_fill_uniform), filled on the device when the
- * request is admitted, and result w = RN(RN(alpha*x) + y) -- the same bits
- * whether it runs alone or batched with any other requests. */
-enum { WXPY_SERVE_BATCHED = 0, WXPY_SERVE_SERIAL = 1 };
+ * for a stream of independent requests.  A seeded request (n, alpha, seed)
+ * gets inputs x, y = U(-1,1) streams (seed, WXPY_TAG_X) and (seed, WXPY_TAG_Y)
+ * of the seeded generator (wxpy_fill_uniform), written into its resident
+ * buffers on the device; a caller-data request (wxpy_server_submit_data) gets
+ * the caller's x and y copied into them.  Either way the result is
+ * w = RN(RN(alpha*x) + y) -- the same bits whether the request runs alone or
+ * batched with any other requests.
+ *
+ * Modes:
+ *   WXPY_SERVE_BATCHED  per batch, the inputs step (one segmented fill launch
+ *                       for the seeded requests, copies for the caller-data
+ *                       ones) and then ONE launch of the batched segmented
+ *                       kernel (the one wxpy_batch runs) over the batch,
+ *                       reading x and y from the resident buffers and writing
+ *                       w: 24 bytes per element;
+ *   WXPY_SERVE_SERIAL   the baseline over the identical data path: per
+ *                       request, the inputs step (fill x, fill y, or the
+ *                       copies) and one wxpy() call;
+ *   WXPY_SERVE_FUSED    seeded requests only: one kernel per batch generates
+ *                       x and y in registers and writes x, y and w, reading
+ *                       nothing (no load path of wxpy is exercised). */
+enum { WXPY_SERVE_BATCHED = 0, WXPY_SERVE_SERIAL = 1, WXPY_SERVE_FUSED = 2 };
+
+/* Where the caller's data of wxpy_server_submit_data lives. */
+enum { WXPY_SERVE_DATA_DEVICE = 0, WXPY_SERVE_DATA_HOST = 1 };
 enum {
     WXPY_REQ_QUEUED = 0,    /* waiting for memory or a slot */
     WXPY_REQ_ADMITTED = 1,  /* buffers assigned, not yet launched */
@@ -619,10 +643,8 @@ typedef struct wxpy_server_config {
                              different streams overlap on the device */
     int32_t max_batch;    /* requests coalesced into one batched launch */
     int32_t max_queue;    /* queued requests beyond which submit refuses (EBUSY) */
-    int32_t mode;         /* WXPY_SERVE_BATCHED: one segmented launch per batch
-                             that generates the inputs and computes w;
-                             WXPY_SERVE_SERIAL: per-request launches (fill x,
-                             fill y, wxpy()), the baseline */
+    int32_t mode;         /* WXPY_SERVE_BATCHED, WXPY_SERVE_SERIAL (the
+                             baseline) or WXPY_SERVE_FUSED; see above */
     int32_t admission;    /* 0: strict arrival order -- a request that does not
                              fit the arena waits, and nothing passes it;
                              > 0: backfill -- while the queue's head does not
@@ -662,13 +684,27 @@ int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out);
 int wxpy_server_submit(wxpy_server *sv, int64_t n, double alpha, uint64_t seed,
                        uint64_t *ticket);
 
+/* Queues a request on the caller's own data: x and y, n doubles each, in
+ * device memory (kind WXPY_SERVE_DATA_DEVICE) or host memory
+ * (WXPY_SERVE_DATA_HOST; pinned memory lets the copies run asynchronously,
+ * pageable memory works but stalls the scheduler while it copies).  When the
+ * request's batch runs, the server copies x and y into the request's resident
+ * buffers on that batch's stream, ahead of the batch's kernel.  The caller
+ * keeps x and y valid and unchanged until the request is done or failed;
+ * the server never writes them.  Errors as wxpy_server_submit, plus
+ * WXPY_EINVAL for a bad kind, a null or non-8-byte-aligned pointer, or a
+ * server in WXPY_SERVE_FUSED mode. */
+int wxpy_server_submit_data(wxpy_server *sv, int64_t n, double alpha, const double *x,
+                            const double *y, int kind, uint64_t *ticket);
+
 /* State (WXPY_REQ_*) and, once done or failed, the submit -> completion
  * latency in seconds (-1 before).  WXPY_ENOTFOUND for an unknown or released
  * ticket. */
 int wxpy_server_poll(wxpy_server *sv, uint64_t ticket, int *state, double *latency_s);
 
-/* Blocks until the request is done (WXPY_OK), failed (WXPY_ECUDA) or the
- * timeout passes (WXPY_ETIMEOUT). */
+/* Blocks until the request is done (WXPY_OK), failed (WXPY_ECUDA: a launch
+ * or copy of its batch failed, or the segmented kernel's tile bounds check
+ * fired) or the timeout passes (WXPY_ETIMEOUT). */
 int wxpy_server_wait(wxpy_server *sv, uint64_t ticket, double timeout_s, double *latency_s);
 
 /* Device pointers of a done request's x, y, w and its n; valid until release. */

@@ -174,6 +174,8 @@ SIGNATURES = {
     "wxpy_batch_noalloc": (_INT, [_P, _I64, _P]),
     "wxpy_server_create": (_INT, [_P, ctypes.POINTER(_P)]),
     "wxpy_server_submit": (_INT, [_P, _I64, _D, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "wxpy_server_submit_data": (_INT, [_P, _I64, _D, _P, _P, _INT,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
     "wxpy_server_poll": (_INT, [_P, ctypes.c_uint64, ctypes.POINTER(_INT), ctypes.POINTER(_D)]),
     "wxpy_server_wait": (_INT, [_P, ctypes.c_uint64, _D, ctypes.POINTER(_D)]),
     "wxpy_server_result": (_INT, [_P, ctypes.c_uint64, ctypes.POINTER(_P), ctypes.POINTER(_P),

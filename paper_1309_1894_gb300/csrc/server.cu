@@ -1,6 +1,8 @@
 // server.cu -- a continuous-batching request server for VecWXPY.
 //
-// Clients submit requests (n, alpha, seed).  A scheduler thread
+// Clients submit requests: (n, alpha, seed), whose inputs the server generates
+// on the device, or (n, alpha, x, y) with the caller's own data in device or
+// host memory.  A scheduler thread
 //   1. admits queued requests in arrival order while the device-memory budget
 //      (one arena, first fit, 256-byte blocks holding x, y, w) and the slot
 //      limit allow.  Strict order (admission = 0): a request that does not
@@ -9,21 +11,28 @@
 //      of it, for at most A us of the head's wait -- then the head holds the
 //      line until memory frees, so it cannot starve;
 //   2. coalesces every admitted, not yet launched request (up to max_batch)
-//      into one batch and launches it on the next free stream: one segmented
-//      kernel that generates each request's inputs from its seed and computes
-//      its w in the same pass -- one launch per batch, whatever the number of
-//      requests in it;
+//      into one batch and runs it on the next free stream in two steps:
+//      (a) the inputs are put into the requests' resident buffers -- one
+//      segmented fill launch generates x and y of every seeded request, and
+//      the caller-data requests are copied in;
+//      (b) one launch of the batched segmented kernel (wxpy_seg_kernel, the
+//      same kernel and tile body as wxpy_batch) reads x and y from those
+//      buffers and writes w -- 24 bytes per element, one launch per batch
+//      whatever the number of requests in it;
 //   3. polls the batches' completion events, stamps each request's completion
 //      time, and frees the buffers of requests marked auto-release.
 // Requests that arrive while batches run on other streams are admitted and
 // launched as soon as memory and a stream free up, so their work overlaps on
 // the device (continuous batching, not a queue drained batch by batch).  The
-// serial mode is the baseline: the same steps per request with per-call
-// launches (fill x, fill y, wxpy()) and no coalescing.
+// serial mode is the baseline over the identical data path: per request the
+// same inputs step (fill x and fill y, or the copies) and one wxpy() call,
+// with no coalescing.  The fused mode is a separate option for seeded
+// requests only: one kernel per batch generates x and y in registers and
+// writes x, y and w without reading anything back.
 //
 // Each request's result is element-wise w = RN(RN(alpha*x) + y) on its own
-// inputs x, y = U(-1,1) streams (seed, 1) and (seed, 2) (paper Sec. 3, Fig. 1
-// vecwxpy), so it is the same bits alone and in any mix.
+// inputs (paper Sec. 3, Fig. 1 vecwxpy), so it is the same bits alone and in
+// any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -103,10 +112,17 @@ class Arena {
 
 enum ReqState { kQueued = 0, kAdmitted = 1, kRunning = 2, kDone = 3, kFailed = 4 };
 
+// Request error for a batch whose tile bounds check fired (not a CUDA error code).
+constexpr int kTileCheckFailed = -1;
+
 struct Request {
     int64_t n = 0;
     double alpha = 0;
     uint64_t seed = 0;
+    // Caller data: source pointers and kind (WXPY_SERVE_DATA_*), or -1 for a
+    // seeded request whose inputs the server generates.
+    int src_kind = -1;
+    const double *src_x = nullptr, *src_y = nullptr;
     int state = kQueued;
     bool auto_release = false;
     int64_t off = -1, bytes = 0;
@@ -126,17 +142,24 @@ struct ServePlan {
     int32_t pad;
 };
 
-// A batch in flight on one stream, with its staging (pinned host) and device tables.
+// A batch in flight on one stream, with its staging (pinned host) and device
+// tables: descriptors, the fill plan of the seeded requests, the tile list of
+// the segmented kernel and its status word.
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
     std::vector<uint64_t> tickets;
-    int64_t cap_segs = 0;
+    int64_t cap_segs = 0, cap_tiles = 0;
     wxpy_desc *h_table = nullptr, *d_table = nullptr;
     uint64_t *h_seeds = nullptr, *d_seeds = nullptr;
     ServePlan *h_plan = nullptr, *d_plan = nullptr;
+    TileRec *h_tiles = nullptr, *d_tiles = nullptr;
+    unsigned *h_status = nullptr, *d_status = nullptr;
 };
+
+// Elements per tile of the fill launch (one warp per tile).
+constexpr int64_t kFillTile = 8192;
 
 // Largest s in [lo, count) with plan[s].first_tile <= t (tiles only grow
 // along a warp's sequence, so the previous answer is a valid lower bound).
@@ -225,6 +248,90 @@ __global__ void __launch_bounds__(256) serve_fused_kernel(const wxpy_desc *table
     }
 }
 
+// The inputs step of a batch: for every seeded request, x and y from the
+// request's seed (streams (seed, 1) and (seed, 2), the values
+// wxpy_fill_uniform writes) stored into its resident buffers.  A warp takes a
+// tile of kFillTile elements; a lane writes four consecutive elements as
+// 32-byte vectors (tiles start at multiples of kFillTile in 256-byte-aligned
+// buffers), the ragged end of a tile element by element.  Requests with
+// caller data have no tiles in the plan.  Reads nothing; 16 bytes written per
+// element.
+__global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
+                                                         const uint64_t *seeds,
+                                                         const ServePlan *plan, int64_t count,
+                                                         int64_t ntiles) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t s = 0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        s = find_request(plan, count, t, s);
+        const wxpy_desc d = table[s];
+        const int64_t begin = (t - plan[s].first_tile) * kFillTile;
+        const int64_t end = min(d.n, begin + kFillTile);
+        const uint64_t kx = stream_key_of(seeds[s], 1), ky = stream_key_of(seeds[s], 2);
+        double *x = const_cast<double *>(d.x), *y = const_cast<double *>(d.y);
+        const int64_t nvec = (end - begin) >> 2;
+        for (int64_t c = lane; c < nvec; c += 32) {
+            const int64_t i0 = begin + 4 * c;
+            double xv[4], yv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xv[q] = uniform_pm1(kx, i0 + q);
+                yv[q] = uniform_pm1(ky, i0 + q);
+            }
+            st4_cs(x + i0, xv[0], xv[1], xv[2], xv[3]);
+            st4_cs(y + i0, yv[0], yv[1], yv[2], yv[3]);
+        }
+        for (int64_t i = begin + 4 * nvec + lane; i < end; i += 32) {
+            x[i] = uniform_pm1(kx, i);
+            y[i] = uniform_pm1(ky, i);
+        }
+    }
+}
+
+// Tile list of a batch for the segmented kernel: each request cut into tiles
+// of its size bucket's length (the batch shape, as in wxpy_batch), ordered
+// longest first by power-of-two class of the tile length -- a stable counting
+// sort, linear in the tiles, so that the static round-robin over warps ends
+// on short tiles.  Returns the tile count; writes the tiles only when they
+// fit in `cap`.
+int64_t serve_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape, TileRec *out,
+                     int64_t cap) {
+    int64_t per_class[64] = {0};
+    auto tile_len = [&](int64_t n) {
+        const int b = 63 - __builtin_clzll((unsigned long long)n);
+        const int64_t T = shape.tile_elems[b] > 0 ? shape.tile_elems[b] : n;
+        return std::min<int64_t>(T, kMaxTileElems);
+    };
+    auto cls = [](int64_t len) { return 63 - __builtin_clzll((unsigned long long)len); };
+    int64_t total = 0;
+    for (int64_t s = 0; s < count; ++s) {
+        const int64_t n = t[s].n, T = tile_len(n);
+        per_class[cls(T)] += n / T;
+        if (n % T) per_class[cls(n % T)] += 1;
+        total += (n + T - 1) / T;
+    }
+    if (total > cap) return total;
+    int64_t start[64];
+    int64_t pos = 0;
+    for (int c = 63; c >= 0; --c) {
+        start[c] = pos;
+        pos += per_class[c];
+    }
+    for (int64_t s = 0; s < count; ++s) {
+        const int64_t n = t[s].n, T = tile_len(n);
+        const int b = 63 - __builtin_clzll((unsigned long long)n);
+        const uint32_t ul =
+            (uint32_t)std::min<int>(2, std::max<int>(0, shape.unroll_log2[b])) << 30;
+        for (int64_t b0 = 0; b0 < n; b0 += T) {
+            const int64_t len = std::min<int64_t>(T, n - b0);
+            out[start[cls(len)]++] = TileRec{b0, (int32_t)s, (uint32_t)len | ul};
+        }
+    }
+    return total;
+}
+
 // Saturated Poisson load on GB300 (n log-uniform in [2^8, 2^24]): 2.09e11
 // elements/s with every product in FP64, 1.82e11 with half, 1.59e11 with all
 // in the integer pipelines -- the generator keeps the ALU pipe busy and
@@ -275,34 +382,72 @@ struct wxpy_server {
 namespace wx {
 namespace {
 
+void free_tiles(Slot &s) {
+    if (s.d_tiles) cudaFree(s.d_tiles);
+    if (s.h_tiles) cudaFreeHost(s.h_tiles);
+    s.d_tiles = nullptr;
+    s.h_tiles = nullptr;
+    s.cap_tiles = 0;
+}
+
+// (Re)sizes the slot's tile list for `tiles` records; the slot must be idle.
+cudaError_t ensure_tiles(Slot &s, int64_t tiles) {
+    if (tiles <= s.cap_tiles) return cudaSuccess;
+    free_tiles(s);
+    const int64_t cap = std::max<int64_t>(tiles, 4096);
+    cudaError_t e = cudaMalloc(&s.d_tiles, sizeof(TileRec) * cap);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_tiles, sizeof(TileRec) * cap);
+    if (e != cudaSuccess) {
+        free_tiles(s);
+        return e;
+    }
+    s.cap_tiles = cap;
+    return cudaSuccess;
+}
+
 void free_slot(Slot &s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.d_table) cudaFree(s.d_table);
     if (s.d_seeds) cudaFree(s.d_seeds);
     if (s.d_plan) cudaFree(s.d_plan);
+    if (s.d_status) cudaFree(s.d_status);
     if (s.h_table) cudaFreeHost(s.h_table);
     if (s.h_seeds) cudaFreeHost(s.h_seeds);
     if (s.h_plan) cudaFreeHost(s.h_plan);
+    if (s.h_status) cudaFreeHost(s.h_status);
+    free_tiles(s);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot{};
 }
 
-cudaError_t init_slot(Slot &s, int64_t segs) {
+// `tiles`: initial capacity of the tile list (it grows when a batch needs more).
+cudaError_t init_slot(Slot &s, int64_t segs, int64_t tiles) {
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_table, sizeof(wxpy_desc) * segs);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_seeds, sizeof(uint64_t) * segs);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_plan, sizeof(ServePlan) * segs);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_table, sizeof(wxpy_desc) * segs);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_seeds, sizeof(uint64_t) * segs);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_plan, sizeof(ServePlan) * segs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(s.d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        *s.h_status = 0;
+        e = ensure_tiles(s, tiles);
+    }
     s.cap_segs = segs;
     return e;
 }
 
 // Marks the requests of a finished (or failed) slot; caller holds the lock.
 void retire_slot(wxpy_server *sv, Slot &s, Clock::time_point now, int error) {
+    // A set status word means the segmented kernel skipped a tile that did not
+    // fit its descriptor: the batch's results are incomplete.
+    if (!error && s.h_status && *s.h_status) error = kTileCheckFailed;
+    if (s.h_status) *s.h_status = 0;
     for (uint64_t t : s.tickets) {
         auto it = sv->reqs.find(t);
         if (it == sv->reqs.end()) continue;
@@ -329,54 +474,119 @@ void retire_slot(wxpy_server *sv, Slot &s, Clock::time_point now, int error) {
     sv->cv_done.notify_all();
 }
 
+// Copies a caller-data request's x and y into its resident buffers on `st`.
+cudaError_t copy_in(const Request *r, cudaStream_t st) {
+    const cudaMemcpyKind k =
+        r->src_kind == WXPY_SERVE_DATA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t bytes = (size_t)r->n * 8;
+    cudaError_t e = cudaMemcpyAsync(r->x, r->src_x, bytes, k, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->y, r->src_y, bytes, k, st);
+    return e;
+}
+
 // Launches the requests in `batch` on slot s.  Caller does NOT hold the lock;
 // the requests are already marked running.  Returns a cudaError_t.
 cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> &batch) {
     TraceRange trace("wxpy_server_batch");
     cudaError_t e = cudaSuccess;
     if (sv->cfg.mode == WXPY_SERVE_SERIAL) {
-        // Baseline: the same requests, launched call by call (three launches
-        // per request) instead of coalesced into two launches per batch.
+        // Baseline: the same requests over the same data path, call by call:
+        // the inputs step (fill x, fill y -- or the copies) and one wxpy() per
+        // request, nothing coalesced.
         for (Request *r : batch) {
-            int st = launch_fill_uniform(r->x, r->n, r->seed, 1, 0, -1.0, 1.0, s.stream);
-            if (st == WXPY_OK) st = launch_fill_uniform(r->y, r->n, r->seed, 2, 0, -1.0, 1.0, s.stream);
+            int st = WXPY_OK;
+            if (r->src_kind < 0) {
+                st = launch_fill_uniform(r->x, r->n, r->seed, 1, 0, -1.0, 1.0, s.stream);
+                if (st == WXPY_OK)
+                    st = launch_fill_uniform(r->y, r->n, r->seed, 2, 0, -1.0, 1.0, s.stream);
+                if (st == WXPY_OK) sv->launches += 2;
+            } else if ((e = copy_in(r, s.stream)) != cudaSuccess) {
+                return e;
+            }
             if (st == WXPY_OK) st = wxpy(r->n, r->alpha, r->x, r->y, r->w, s.stream);
             if (st != WXPY_OK) return (cudaError_t)(wxpy_last_cuda_error() ? wxpy_last_cuda_error() : 1);
-            sv->launches += 3;
+            sv->launches += 1;
         }
         return cudaEventRecord(s.done, s.stream);
     }
+    const bool fused = sv->cfg.mode == WXPY_SERVE_FUSED;
     const int64_t count = (int64_t)batch.size();
     const BatchShape shape = current_batch_shape();
-    int64_t ntiles = 0;
+    // Descriptors, and the plan of the generated inputs: the fill's tiles in
+    // the batched mode, the fused kernel's (per-bucket tile length) in the
+    // fused mode; caller-data requests get none.
+    int64_t nplan = 0;
     for (int64_t i = 0; i < count; ++i) {
         const Request *r = batch[i];
         s.h_table[i] = wxpy_desc{r->n, r->alpha, r->x, r->y, r->w};
         s.h_seeds[i] = r->seed;
-        const int b = 63 - __builtin_clzll((unsigned long long)r->n);
-        const int64_t T = std::min<int64_t>(shape.tile_elems[b] > 0 ? shape.tile_elems[b] : r->n,
-                                            kMaxTileElems);
-        s.h_plan[i] = ServePlan{ntiles, T, std::min<int>(2, std::max<int>(0, shape.unroll_log2[b])), 0};
-        ntiles += (r->n + T - 1) / T;
+        int64_t T = kFillTile;
+        int ulog = 0;
+        if (fused) {
+            const int b = 63 - __builtin_clzll((unsigned long long)r->n);
+            T = std::min<int64_t>(shape.tile_elems[b] > 0 ? shape.tile_elems[b] : r->n,
+                                  kMaxTileElems);
+            ulog = std::min<int>(2, std::max<int>(0, shape.unroll_log2[b]));
+        }
+        s.h_plan[i] = ServePlan{nplan, T, ulog, 0};
+        if (r->src_kind < 0) nplan += (r->n + T - 1) / T;
+    }
+    int64_t ntiles = 0;
+    if (!fused) {
+        // The tile list of step (b), before anything of this batch is queued:
+        // the slot is idle (its last batch completed), so a list too short
+        // for this batch can be resized here.
+        ntiles = serve_tiles(s.h_table, count, shape, s.h_tiles, s.cap_tiles);
+        if (ntiles > s.cap_tiles) {
+            if ((e = ensure_tiles(s, ntiles + ntiles / 4)) != cudaSuccess) return e;
+            ntiles = serve_tiles(s.h_table, count, shape, s.h_tiles, s.cap_tiles);
+        }
     }
     e = cudaMemcpyAsync(s.d_table, s.h_table, sizeof(wxpy_desc) * count, cudaMemcpyHostToDevice,
                         s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.d_seeds, s.h_seeds, sizeof(uint64_t) * count, cudaMemcpyHostToDevice,
-                            s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.d_plan, s.h_plan, sizeof(ServePlan) * count, cudaMemcpyHostToDevice,
-                            s.stream);
+    if (e == cudaSuccess && nplan > 0)
+        e = cudaMemcpyAsync(s.d_seeds, s.h_seeds, sizeof(uint64_t) * count,
+                            cudaMemcpyHostToDevice, s.stream);
+    if (e == cudaSuccess && nplan > 0)
+        e = cudaMemcpyAsync(s.d_plan, s.h_plan, sizeof(ServePlan) * count,
+                            cudaMemcpyHostToDevice, s.stream);
     if (e != cudaSuccess) return e;
     const int64_t wpb = 256 / 32;
-    const unsigned grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)8 * sv->sm_count, (ntiles + wpb - 1) / wpb));
-    e = injected_launch_error();
+    if (fused) {
+        const unsigned grid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)8 * sv->sm_count, (nplan + wpb - 1) / wpb));
+        e = injected_launch_error();
+        if (e != cudaSuccess) return e;
+        serve_fused_kernel<kServePM><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan,
+                                                                 count, nplan);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sv->launches += 1;
+        return cudaEventRecord(s.done, s.stream);
+    }
+    // (a) inputs into the resident buffers
+    for (const Request *r : batch)
+        if (r->src_kind >= 0 && (e = copy_in(r, s.stream)) != cudaSuccess) return e;
+    if (nplan > 0) {
+        const unsigned grid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)8 * sv->sm_count, (nplan + wpb - 1) / wpb));
+        e = injected_launch_error();
+        if (e != cudaSuccess) return e;
+        serve_fill_kernel<<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
+                                                      nplan);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sv->launches += 1;
+    }
+    // (b) one segmented launch over the batch: reads x, y, writes w; its
+    // status word starts at zero and comes back with the batch
+    e = cudaMemcpyAsync(s.d_tiles, s.h_tiles, sizeof(TileRec) * ntiles, cudaMemcpyHostToDevice,
+                        s.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_status, 0, sizeof(unsigned), s.stream);
     if (e != cudaSuccess) return e;
-    serve_fused_kernel<kServePM><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
-                                                             ntiles);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_segmented(s.d_table, s.d_tiles, ntiles, s.d_status, shape, sv->sm_count, s.stream);
+    if (e != cudaSuccess) return e;
     sv->launches += 1;
+    e = cudaMemcpyAsync(s.h_status, s.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s.stream);
+    if (e != cudaSuccess) return e;
     return cudaEventRecord(s.done, s.stream);
 }
 
@@ -526,7 +736,8 @@ void scheduler(wxpy_server *sv) {
 }
 
 int submit_locked(wxpy_server *sv, int64_t n, double alpha, uint64_t seed, bool auto_release,
-                  uint64_t *ticket) {
+                  uint64_t *ticket, int src_kind = -1, const double *src_x = nullptr,
+                  const double *src_y = nullptr) {
     if (n <= 0) return fail(WXPY_EINVAL, "request needs n > 0");
     const int64_t bytes = 3 * round_up(n * 8, kBlock);
     if (n > (int64_t)1 << 40 || bytes > sv->arena.size())
@@ -541,6 +752,9 @@ int submit_locked(wxpy_server *sv, int64_t n, double alpha, uint64_t seed, bool 
     r.n = n;
     r.alpha = alpha;
     r.seed = seed;
+    r.src_kind = src_kind;
+    r.src_x = src_x;
+    r.src_y = src_y;
     r.auto_release = auto_release;
     r.t_submit = Clock::now();
     sv->queue.push_back(t);
@@ -567,7 +781,9 @@ int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out) {
     *out = nullptr;
     if (cfg->budget_bytes < 3 * kBlock || cfg->max_slots < 1 || cfg->n_streams < 1 ||
         cfg->n_streams > 16 || cfg->max_batch < 1 || cfg->max_queue < 1 ||
-        (cfg->mode != WXPY_SERVE_BATCHED && cfg->mode != WXPY_SERVE_SERIAL) || cfg->admission < 0)
+        (cfg->mode != WXPY_SERVE_BATCHED && cfg->mode != WXPY_SERVE_SERIAL &&
+         cfg->mode != WXPY_SERVE_FUSED) ||
+        cfg->admission < 0)
         return fail(WXPY_EINVAL, "bad server configuration");
     int st = WXPY_OK;
     const DeviceProps *dp = current_device(&st);
@@ -584,9 +800,13 @@ int wxpy_server_create(const wxpy_server_config *cfg, wxpy_server **out) {
     }
     sv->arena.init(cfg->budget_bytes);
     const int64_t segs = std::min<int64_t>(cfg->max_batch, cfg->max_slots);
+    // Tile list: room for a batch of its stream's share of the budget at the
+    // default tile length, plus one ragged tile per request; a batch that
+    // needs more (shorter tuned tiles) grows it.
+    const int64_t tiles = cfg->budget_bytes / cfg->n_streams / (24 * 8192) + segs;
     sv->slots.resize((size_t)cfg->n_streams);
     for (Slot &s : sv->slots) {
-        e = init_slot(s, segs);
+        e = init_slot(s, segs, tiles);
         if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
@@ -605,6 +825,23 @@ int wxpy_server_submit(wxpy_server *sv, int64_t n, double alpha, uint64_t seed, 
     if (!sv || !ticket) return fail(WXPY_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(sv->mu);
     const int st = submit_locked(sv, n, alpha, seed, false, ticket);
+    if (st == WXPY_OK) sv->cv_submit.notify_one();
+    return st;
+}
+
+int wxpy_server_submit_data(wxpy_server *sv, int64_t n, double alpha, const double *x,
+                            const double *y, int kind, uint64_t *ticket) {
+    if (!sv || !ticket) return fail(WXPY_EINVAL, "null argument");
+    if (kind != WXPY_SERVE_DATA_DEVICE && kind != WXPY_SERVE_DATA_HOST)
+        return fail(WXPY_EINVAL, "data kind %d is neither device (0) nor host (1)", kind);
+    if (n > 0 && (!x || !y)) return fail(WXPY_EINVAL, "null input pointer");
+    if ((((uintptr_t)x) | ((uintptr_t)y)) & 7u)
+        return fail(WXPY_EINVAL, "input pointers must be 8-byte aligned");
+    if (sv->cfg.mode == WXPY_SERVE_FUSED)
+        return fail(WXPY_EINVAL, "the fused mode generates its inputs: caller data needs the "
+                                 "batched or serial mode");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int st = submit_locked(sv, n, alpha, 0, false, ticket, kind, x, y);
     if (st == WXPY_OK) sv->cv_submit.notify_one();
     return st;
 }
@@ -630,8 +867,11 @@ int wxpy_server_wait(wxpy_server *sv, uint64_t ticket, double timeout_s, double 
         if (it == sv->reqs.end()) return fail(WXPY_ENOTFOUND, "unknown ticket");
         if (it->second.state >= kDone) {
             if (latency_s) *latency_s = seconds(it->second.t_done - it->second.t_submit);
-            if (it->second.state == kFailed)
+            if (it->second.state == kFailed) {
+                if (it->second.error == kTileCheckFailed)
+                    return fail(WXPY_ECUDA, "request failed: the batch's tile bounds check fired");
                 return fail(WXPY_ECUDA, "request failed with CUDA error %d", it->second.error);
+            }
             return WXPY_OK;
         }
         if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&

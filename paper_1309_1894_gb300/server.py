@@ -9,7 +9,8 @@ import ctypes
 
 from .binding import _D, _I64, _P, check, lib
 
-SERVE_BATCHED, SERVE_SERIAL = 0, 1
+SERVE_BATCHED, SERVE_SERIAL, SERVE_FUSED = 0, 1, 2
+DATA_DEVICE, DATA_HOST = 0, 1
 REQ_QUEUED, REQ_ADMITTED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3, 4
 
 
@@ -65,6 +66,25 @@ class Server:
         t = ctypes.c_uint64()
         check(lib().wxpy_server_submit(self.handle, n, float(alpha), seed & ((1 << 64) - 1),
                                        ctypes.byref(t)), "wxpy_server_submit")
+        return t.value
+
+    def submit_data(self, alpha: float, x, y) -> int:
+        """Queue a request on the caller's data: float64 1-D contiguous tensors
+        x and y (same length), both on the GPU or both in host memory.  They
+        must stay alive and unchanged until the request is done or failed."""
+        if x.dtype != y.dtype or str(x.dtype) != "torch.float64":
+            raise TypeError("x and y must be float64 tensors")
+        if x.dim() != 1 or y.dim() != 1 or not x.is_contiguous() or not y.is_contiguous():
+            raise ValueError("x and y must be contiguous 1-D tensors")
+        if x.numel() != y.numel():
+            raise ValueError("x and y must have the same length")
+        if x.is_cuda != y.is_cuda:
+            raise ValueError("x and y must both be device or both be host tensors")
+        kind = DATA_DEVICE if x.is_cuda else DATA_HOST
+        t = ctypes.c_uint64()
+        check(lib().wxpy_server_submit_data(self.handle, x.numel(), float(alpha), x.data_ptr(),
+                                            y.data_ptr(), kind, ctypes.byref(t)),
+              "wxpy_server_submit_data")
         return t.value
 
     def poll(self, ticket: int) -> tuple[int, float]:

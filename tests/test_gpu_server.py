@@ -1,9 +1,12 @@
 """GPU tests of the continuous-batching server through the C ABI.
 
 Each request's result must be the same bits alone and in the mix (0 ULP):
-equal to a standalone wxpy() on the same seeded inputs, and to the oracle.
-The server's admission (budget, slots, queue limit), failure reporting and
-built-in Poisson client are checked too.
+equal to a standalone wxpy() on the same seeded inputs, and to the oracle --
+for seeded requests and for requests on the caller's own data (device or
+host memory), in the batched mode (inputs step, then one segmented launch
+that reads x and y from the resident buffers), the serial baseline and the
+fused option.  The server's admission (budget, slots, queue limit), failure
+reporting and built-in Poisson client are checked too.
 """
 import numpy as np
 import pytest
@@ -12,8 +15,8 @@ import torch
 import oracle
 import paper_1309_1894_gb300 as wx
 from paper_1309_1894_gb300 import synth
-from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL, REQ_DONE, \
-    REQ_QUEUED, REQ_FAILED
+from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL, SERVE_FUSED, \
+    REQ_DONE, REQ_QUEUED, REQ_FAILED
 
 pytestmark = pytest.mark.gpu
 
@@ -77,17 +80,106 @@ def test_batched_results_equal_alone_and_oracle():
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (n, s)
 
 
-def test_serial_and_batched_modes_agree():
+def test_serial_batched_and_fused_modes_agree():
     reqs = request_mix(32, 80, 1 << 16)
     a, st_a = run_requests(SERVE_BATCHED, reqs, n_streams=3, max_batch=16)
     b, st_b = run_requests(SERVE_SERIAL, reqs, n_streams=1, max_batch=1)
     c, st_c = run_requests(SERVE_SERIAL, reqs, n_streams=2, max_batch=32)
+    f, st_f = run_requests(SERVE_FUSED, reqs, n_streams=2, max_batch=16)
     assert st_b["batches"] == len(reqs) and st_b["mean_batch"] == 1.0
+    # serial: fill x, fill y, wxpy() per request
     assert st_b["launches"] == 3 * len(reqs) == st_c["launches"]
-    assert st_a["launches"] == st_a["batches"]  # one fused launch per batch
+    # batched: one fill launch and one segmented launch per batch
+    assert st_a["launches"] == 2 * st_a["batches"] and st_a["batches"] < len(reqs)
+    assert st_f["launches"] == st_f["batches"]  # fused: one launch per batch
     for (_, _, s) in reqs:
         assert torch.equal(a[s].view(torch.int64), b[s].view(torch.int64))
         assert torch.equal(a[s].view(torch.int64), c[s].view(torch.int64))
+        assert torch.equal(a[s].view(torch.int64), f[s].view(torch.int64))
+
+
+@pytest.mark.parametrize("mode", [SERVE_BATCHED, SERVE_SERIAL])
+def test_caller_data_requests_in_a_mix(mode):
+    """Requests on the caller's data -- device tensors and pinned host tensors
+    -- mixed with seeded requests in the same batches: every result is the
+    oracle's on its own inputs, the caller's buffers are untouched, and the
+    resident x and y hold exactly the caller's values."""
+    rng = np.random.default_rng(41)
+    lens = [1, 5, 4099, 8192, 70001, (1 << 18) + 3, 300000]
+    data = []
+    for i, n in enumerate(lens):
+        xh = synth.uniform_pm1(900 + i, synth.TAG_X, n)
+        yh = synth.uniform_pm1(900 + i, synth.TAG_Y, n)
+        # special values in the caller's data: signed zeros, a subnormal, an infinity
+        if n > 8:
+            xh[:4] = [0.0, -0.0, 5e-324, np.inf]
+            yh[:4] = [-0.0, 0.0, -5e-324, 1.0]
+        alpha = float(rng.uniform(-2, 2))
+        on_gpu = i % 2 == 0
+        if on_gpu:
+            x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+        else:
+            x = torch.from_numpy(xh).pin_memory()
+            y = torch.from_numpy(yh).pin_memory()
+        data.append((n, alpha, xh, yh, x, y))
+    seeded = request_mix(43, 30, 1 << 17)
+    with Server(budget_bytes=1 << 30, mode=mode, n_streams=2, max_batch=16) as sv:
+        tickets = []
+        for k in range(max(len(data), len(seeded))):
+            if k < len(data):
+                n, a, _, _, x, y = data[k]
+                tickets.append(("d", k, sv.submit_data(a, x, y)))
+            if k < len(seeded):
+                n, a, sd = seeded[k]
+                tickets.append(("s", k, sv.submit(n, a, sd)))
+        for _, _, t in tickets:
+            sv.wait(t, 60.0)
+        torch.cuda.synchronize()
+        for kind, k, t in tickets:
+            m, px, py, pw = sv.result(t)
+            if kind == "d":
+                n, a, xh, yh, x, y = data[k]
+                assert m == n
+                got = _from_ptr(pw, n).cpu().numpy()
+                want = oracle.wxpy(a, xh, yh)
+                assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (n, k)
+                assert np.array_equal(_from_ptr(px, n).cpu().numpy().view(np.uint64),
+                                      xh.view(np.uint64))
+                assert np.array_equal(_from_ptr(py, n).cpu().numpy().view(np.uint64),
+                                      yh.view(np.uint64))
+                assert np.array_equal(x.cpu().numpy().view(np.uint64), xh.view(np.uint64))
+            else:
+                n, a, sd = seeded[k]
+                assert m == n
+                assert torch.equal(_from_ptr(pw, n).view(torch.int64),
+                                   alone(n, a, sd).view(torch.int64)), (n, sd)
+            sv.release(t)
+        st = sv.stats()
+        assert st["completed"] == len(tickets) and st["failed"] == 0
+        assert st["arena_used"] == 0
+        if mode == SERVE_BATCHED:
+            assert st["batches"] < len(tickets)
+
+
+def test_caller_data_refused_where_invalid():
+    x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with Server(budget_bytes=64 << 20, mode=SERVE_FUSED) as sv:
+        with pytest.raises(wx.WxpyError) as e:
+            sv.submit_data(1.0, x, x)
+        assert e.value.status == wx.WXPY_EINVAL
+    with Server(budget_bytes=64 << 20) as sv:
+        import ctypes
+        t = ctypes.c_uint64()
+        lib = wx.lib()
+        p = x.data_ptr()
+        assert lib.wxpy_server_submit_data(sv.handle, 16, 1.0, p + 4, p, 0, ctypes.byref(t)) \
+            == wx.WXPY_EINVAL
+        assert lib.wxpy_server_submit_data(sv.handle, 16, 1.0, p, p, 2, ctypes.byref(t)) \
+            == wx.WXPY_EINVAL
+        assert lib.wxpy_server_submit_data(sv.handle, 16, 1.0, None, p, 0, ctypes.byref(t)) \
+            == wx.WXPY_EINVAL
+        assert lib.wxpy_server_submit_data(sv.handle, 3 << 20, 1.0, p, p, 0, ctypes.byref(t)) \
+            == wx.WXPY_EBUDGET
 
 
 def test_budget_slots_and_queue_limit():
