@@ -17,10 +17,13 @@
 //   2. a grid maps every tile to its segment and index (binary search);
 //   3. a persistent grid of warps runs the tiles, as the batched kernel does.
 // Descriptors with n <= 0, or with a null or misaligned pointer, get no
-// tiles: they are skipped, never dereferenced.
+// tiles: they are skipped, never dereferenced.  Nothing else is checked: the
+// caller guarantees that within each descriptor w is x, is y, or overlaps
+// neither, and that no descriptor writes what another one reads or writes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -186,9 +189,32 @@ __global__ void __launch_bounds__(256, 2) na_run_kernel(const wxpy_desc *table, 
 }
 
 constexpr int kMaxDev = 64;
-std::once_flag g_na_once[kMaxDev];
-void *g_na_ptr[kMaxDev];
-cudaError_t g_na_err[kMaxDev];
+// Device address of the scratch array per device: null until a lookup has
+// succeeded.  Only a successful lookup is kept, so a lookup that failed (a
+// first call made during a stream capture, or with an error pending) is
+// simply tried again by the next call.
+std::atomic<void *> g_na_ptr[kMaxDev];
+std::mutex g_na_mu;
+
+// The scratch's device address on device `dev` (current); nullptr and the
+// error recorded when the lookup fails.
+NaScratch *scratch_address(int dev, int *status) {
+    void *p = g_na_ptr[dev].load(std::memory_order_acquire);
+    if (p) return (NaScratch *)p;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    p = g_na_ptr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();  // clear a non-sticky error; the next call retries
+            *status = fail_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                                "cudaGetSymbolAddress(scratch)");
+            return nullptr;
+        }
+        g_na_ptr[dev].store(p, std::memory_order_release);
+    }
+    return (NaScratch *)p;
+}
 
 }  // namespace
 }  // namespace wx
@@ -210,13 +236,10 @@ extern "C" int wxpy_batch_noalloc(const wxpy_desc *dev_table, int64_t count, voi
     if (!dp) return st;
     const int dev = dp->device;
     if (dev >= kMaxDev) return fail(WXPY_EINVAL, "device ordinal %d out of range", dev);
-    // Once per device, with that device current: the device address of the
-    // scratch array.
-    std::call_once(g_na_once[dev], [dev] {
-        g_na_err[dev] = cudaGetSymbolAddress(&g_na_ptr[dev], g_noalloc_scratch);
-    });
-    if (g_na_err[dev] != cudaSuccess) return fail_cuda(g_na_err[dev], "cudaGetSymbolAddress(scratch)");
-    auto *sc = (NaScratch *)g_na_ptr[dev];
+    // With the device current: the device address of the scratch array,
+    // looked up on the first successful call for this device.
+    NaScratch *sc = scratch_address(dev, &st);
+    if (!sc) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = injected_launch_error();
     if (e == cudaSuccess) {
