@@ -194,6 +194,21 @@ int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, doubl
  * (direct = 0, or unmapped memory) the staged pipeline above. */
 int wxpy_host_config(int64_t chunk_elems, int slots, int direct);
 
+/* Programmatic dependent launch of the single-call kernels (wxpy, wxpy_host's
+ * kernels, wxpy_run_variant, the searches' candidates).  When on (the
+ * default; the environment variable WXPY_PDL=0 starts the process with it
+ * off), each kernel is launched with programmatic stream serialisation: it
+ * may be scheduled while the previous kernel of its stream is still running,
+ * waits on the device until that kernel has completed and its writes are
+ * visible before touching memory, and lets the next launch be scheduled once
+ * all its blocks have started.  Results and stream ordering are unchanged
+ * (every call still sees all effects of earlier work on its stream); the
+ * launch latency of back-to-back calls overlaps the previous kernel's tail.
+ * enable = 1 on, 0 off, -1 leaves it as it is; *previous (if not NULL) gets
+ * the setting before the call (0 or 1).  WXPY_EINVAL for another enable.
+ * Process-wide; host only. */
+int wxpy_launch_pdl(int enable, int *previous);
+
 /* The same operation with variant `id` (the tuner's and the tests' entry).
  * The variant is adjusted to the call's class as described at wxpy_lookup. */
 int wxpy_run_variant(int id, int64_t n, double alpha, const double *x,

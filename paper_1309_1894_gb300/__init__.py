@@ -19,7 +19,7 @@ from .binding import (  # noqa: F401
     VEC_AXPBYPCZ, VEC_PMULT, VEC_AXPBY, VEC_CLASSES, VEC_CLASS_NAMES,
     wxpy_reference, wxpy_lookup, wxpy_classify,
     wxpy_device_query, wxpy_variant_count, wxpy_variant_describe, wxpy_variant_encode,
-    wxpy_set_variant, wxpy_debug_inject_launch_error, wxpy_fill_uniform,
+    wxpy_set_variant, wxpy_debug_inject_launch_error, wxpy_fill_uniform, wxpy_launch_pdl,
     wxpy_tune, tune, wxpy_tune_get, wxpy_tune_set, wxpy_tune_clear, wxpy_tune_cache_save,
     wxpy_tune_cache_load,
     TUNE_ALIGN16, TUNE_ALIGN8, TUNE_XY, TUNE_WALIAS, TUNE_QUICK, TUNE_RESIDENT,
@@ -30,4 +30,4 @@ from .binding import (  # noqa: F401
     WXPY_OK, WXPY_EINVAL, WXPY_EOVERLAP, WXPY_ENOMEM, WXPY_EBUDGET, WXPY_ECUDA,
     WXPY_ETIMEOUT, WXPY_ENOTFOUND, WXPY_EBUSY, WXPY_EMISMATCH,
 )
-from .server import Server, SERVE_BATCHED, SERVE_SERIAL  # noqa: F401,E402
+from .server import Server, SERVE_BATCHED, SERVE_SERIAL, SERVE_FUSED  # noqa: F401,E402

@@ -125,6 +125,7 @@ SIGNATURES = {
     "wxpy_run_variant": (_INT, [_INT, _I64, _D, _P, _P, _P, _P]),
     "wxpy_reference": (_INT, [_I64, _D, _P, _P, _P, _P]),
     "wxpy_debug_inject_launch_error": (_INT, [_INT, _INT]),
+    "wxpy_launch_pdl": (_INT, [_INT, ctypes.POINTER(_INT)]),
     "wxpy_tune": (_INT, [_I64, ctypes.c_uint, ctypes.POINTER(TuneResult)]),
     "wxpy_tune_get": (_INT, [_INT, ctypes.POINTER(_INT)]),
     "wxpy_tune_set": (_INT, [_INT, _INT]),
@@ -561,6 +562,14 @@ def wxpy_fill_uniform(dst, seed: int, tag: int, lo: float = -1.0, hi: float = 1.
     check(lib().wxpy_fill_uniform(n, seed & ((1 << 64) - 1), tag, start, lo, hi, p,
                                   _stream_handle(stream)), "wxpy_fill_uniform")
     return dst
+
+
+def wxpy_launch_pdl(enable: int = -1) -> int:
+    """Programmatic dependent launch of the single-call kernels: 1 on, 0 off,
+    -1 unchanged; returns the setting before the call."""
+    prev = _INT()
+    check(lib().wxpy_launch_pdl(int(enable), ctypes.byref(prev)), "wxpy_launch_pdl")
+    return prev.value
 
 
 def wxpy_debug_inject_launch_error(cuda_error: int, count: int) -> None:

@@ -51,6 +51,23 @@ DeviceProps g_dev[kMaxDevices];
 cudaError_t g_dev_err[kMaxDevices];
 }  // namespace
 
+namespace {
+// Programmatic dependent launch of the single-call kernels: on unless the
+// environment says WXPY_PDL=0; wxpy_launch_pdl() changes it.
+std::atomic<int> g_pdl{-1};
+}  // namespace
+
+bool pdl_enabled() {
+    int v = g_pdl.load(std::memory_order_relaxed);
+    if (v < 0) {
+        const char *e = std::getenv("WXPY_PDL");
+        v = (e && e[0] == '0') ? 0 : 1;
+        int expected = -1;
+        if (!g_pdl.compare_exchange_strong(expected, v)) v = expected;
+    }
+    return v != 0;
+}
+
 bool trace_enabled() {
     static const bool on = [] {
         const char *v = std::getenv("WXPY_NVTX");
@@ -533,6 +550,14 @@ int wxpy_reference(int64_t n, double alpha, const double *x, const double *y, do
     cudaError_t e = injected_launch_error();
     if (e == cudaSuccess) e = launch_reference((unsigned)grid, 256u, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "reference kernel launch");
+    return WXPY_OK;
+}
+
+int wxpy_launch_pdl(int enable, int *previous) {
+    if (enable < -1 || enable > 1) return fail(WXPY_EINVAL, "enable must be 0, 1 or -1");
+    const int prev = pdl_enabled() ? 1 : 0;
+    if (enable >= 0) g_pdl.store(enable);
+    if (previous) *previous = prev;
     return WXPY_OK;
 }
 

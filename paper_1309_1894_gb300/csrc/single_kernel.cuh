@@ -189,9 +189,24 @@ constexpr int max_threads() {
     return regs <= 64 ? 1024 : (regs <= 128 ? 512 : 256);
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation may start while the previous kernel of
+// its stream is still running; it waits here until that kernel has completed
+// and its memory operations are visible (a no-op for a launch without the
+// attribute), and then lets the next launch of the stream be scheduled: once
+// every block of this grid has passed this point, the next kernel's blocks
+// can take the SMs this grid frees, so its launch overlaps this grid's tail.
+// No memory is touched before the wait, so any dependence between calls (w of
+// one call is x of the next) is kept.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
 __global__ void __launch_bounds__(max_threads<VW, U, GS, XY, EMU>())
     wxpy_single_kernel(const SingleArgs a) {
+    pdl_enter();
     const int64_t tpb = blockDim.x;
     if constexpr (GS == 0) {
         const int64_t c0 = (int64_t)blockIdx.x * tpb * U + threadIdx.x;
@@ -217,10 +232,30 @@ struct SingleEntry {
     int max_threads;        // launch bound of the instance
 };
 
+// Whether launches of the single-call kernels ask for programmatic stream
+// serialisation (api.cu; default on, WXPY_PDL=0 or wxpy_launch_pdl(0) off).
+bool pdl_enabled();
+
+// <<<grid, tpb, 0, s>>>, with the programmatic-serialisation attribute when on.
+template <typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Args...), unsigned grid, unsigned tpb, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tpb);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
 cudaError_t launch_single(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s) {
-    wxpy_single_kernel<VW, U, GS, CACHE, XY, EMU><<<grid, tpb, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(&wxpy_single_kernel<VW, U, GS, CACHE, XY, EMU>, grid, tpb, s, a);
 }
 
 template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
