@@ -637,7 +637,8 @@ def tune_buckets(wx, args, torch):
             rows.append({"k": k, "group": group, "variant": r["best"], "us": r["best_us"],
                          "default_us": r["default_us"], "reference_us": r["reference_us"],
                          "gbs": r["best_gbs"], "candidates": r["candidates"],
-                         "rejected": r["rejected"], "launch_bound": r.get("launch_bound")})
+                         "rejected": r["rejected"], "ties": r["ties"],
+                         "launch_bound": r["launch_bound"]})
     torch.cuda.synchronize()
     if args.tune_cache:
         wx.wxpy_tune_cache_save(args.tune_cache)

@@ -528,6 +528,13 @@ typedef struct wxpy_tune_result {
     int32_t rejected;        /* variants whose output differed from the reference */
     int32_t bucket;          /* floor(log2 n) */
     int32_t tune_key;        /* the cell written */
+    int32_t ties;            /* candidates timed within 3 % of the fastest */
+    int32_t launch_bound;    /* 1: even the plain reference variant timed within
+                                3 % of the fastest, so no kernel shape changes the
+                                call's time (launch and completion dominate); the
+                                cell then gets a fixed choice -- the first
+                                candidate in search order within 3 % -- instead of
+                                a pick among ties; saved in the tune cache */
 } wxpy_tune_result;
 
 /* Runs the search of Sec. 2 for the cell of size bucket floor(log2 n) and the

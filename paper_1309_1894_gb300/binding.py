@@ -62,7 +62,8 @@ class TuneResult(ctypes.Structure):
                 ("default_us", ctypes.c_double), ("reference_us", ctypes.c_double),
                 ("best_gbs", ctypes.c_double), ("candidates", ctypes.c_int32),
                 ("rejected", ctypes.c_int32), ("bucket", ctypes.c_int32),
-                ("tune_key", ctypes.c_int32)]
+                ("tune_key", ctypes.c_int32), ("ties", ctypes.c_int32),
+                ("launch_bound", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "best"}

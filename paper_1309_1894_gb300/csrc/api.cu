@@ -228,10 +228,12 @@ Variant default_variant(const CallClass &c, int64_t n) {
 
 std::atomic<int> g_forced_variant{-1};
 std::atomic<int> g_tuned[kTuneKeys];
+std::atomic<int> g_tuned_launch_bound[kTuneKeys];
 namespace {
 struct TunedInit {
     TunedInit() {
         for (auto &t : g_tuned) t.store(-1, std::memory_order_relaxed);
+        for (auto &t : g_tuned_launch_bound) t.store(0, std::memory_order_relaxed);
     }
 } g_tuned_init;
 }  // namespace

@@ -71,6 +71,8 @@ Variant default_variant(const CallClass &c, int64_t n);
 // Tuning table (flat variant ids, -1 = none) and the forced id.
 extern std::atomic<int> g_forced_variant;
 extern std::atomic<int> g_tuned[kTuneKeys];
+// 1 where the search found the cell launch-bound (its choice fixed, not a pick among ties).
+extern std::atomic<int> g_tuned_launch_bound[kTuneKeys];
 
 // ---- launching ----
 // Runs the (already adjusted) variant on stream s.  Handles the stream split.

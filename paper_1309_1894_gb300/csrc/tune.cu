@@ -245,6 +245,7 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
     }
 
     int candidates = 0, rejected = 0;
+    std::vector<Candidate> all;  // every timed candidate, in search order
     auto consider = [&](const Variant &raw, std::vector<Candidate> &pool) -> int {
         const Variant v = adjust_variant(raw, p.cls);
         for (const auto &c : pool)
@@ -260,6 +261,7 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
         double us = 0;
         if ((s2 = time_variant(v, p, sc, reps, flush, &us)) != WXPY_OK) return s2;
         pool.push_back(Candidate{v, us});
+        all.push_back(Candidate{v, us});
         return WXPY_OK;
     };
     auto best_of = [](const std::vector<Candidate> &pool) {
@@ -325,8 +327,30 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
         chosen = dv;
         chosen_us = def_us;
     }
+    // Launch-bound cells.  When even the plain reference variant (one element
+    // per thread, scalar accesses) times within kTieBand of the winner, no
+    // kernel shape changes the call's time: it is the cost of launching and
+    // finishing a kernel, not of moving its bytes, and the "winner" is a pick
+    // among ties that the timing noise decides.  Such a cell gets a fixed
+    // choice instead: the first candidate in search order (the plainest
+    // shapes come first) whose time is within the band.
+    constexpr double kTieBand = 1.03;
+    const double floor_us = std::min(chosen_us, best.us);
+    int ties = 0;
+    for (const auto &c : all)
+        if (c.us <= floor_us * kTieBand) ++ties;
+    const bool launch_bound = ref_us <= floor_us * kTieBand;
+    if (launch_bound) {
+        for (const auto &c : all)
+            if (c.us <= floor_us * kTieBand) {
+                chosen = c.v;
+                chosen_us = c.us;
+                break;
+            }
+    }
     const int id = encode_variant(chosen);
     g_tuned[p.cls.tune_key].store(id);
+    g_tuned_launch_bound[p.cls.tune_key].store(launch_bound ? 1 : 0);
     if (out) {
         std::memset(out, 0, sizeof *out);
         to_info(chosen, id, &out->best);
@@ -339,6 +363,8 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
         out->rejected = rejected;
         out->bucket = p.cls.bucket;
         out->tune_key = p.cls.tune_key;
+        out->ties = ties;
+        out->launch_bound = launch_bound ? 1 : 0;
     }
     return WXPY_OK;
 }
@@ -441,15 +467,15 @@ int cache_save(const char *path) {
         if (id < 0) continue;
         Variant v;
         decode_variant(id, &v);
-        char buf[360];
+        char buf[400];
         std::snprintf(buf, sizeof buf,
                       "%s\n    {\"key\": %d, \"bucket\": %d, \"align\": %d, \"group\": %d, "
                       "\"variant\": %d, \"vec_bytes\": %d, \"unroll\": %d, \"threads\": %d, "
                       "\"blocks_per_sm\": %d, \"cache\": %d, \"carveout\": %d, \"streams\": %d, "
-                      "\"fp64_offload\": %d}",
+                      "\"fp64_offload\": %d, \"launch_bound\": %d}",
                       first ? "" : ",", k, k / 12, (k / 4) % 3 == 0 ? 32 : ((k / 4) % 3 == 1 ? 16 : 8),
                       k % 4, id, v.vec_bytes, v.unroll, v.threads, v.blocks_per_sm, v.cache,
-                      v.carveout, v.streams, v.offload);
+                      v.carveout, v.streams, v.offload, g_tuned_launch_bound[k].load());
         out += buf;
         first = false;
     }
@@ -481,6 +507,7 @@ int cache_load(const char *path, const char *expect_device) {
                     expect_device);
     // Parse every entry first; apply only if all are valid.
     std::vector<std::pair<int, int>> entries;
+    std::vector<int> entry_lb;  // launch_bound of each entry (0 when the file has none)
     size_t p = s.find("\"entries\"");
     if (p == std::string::npos) return fail(WXPY_EINVAL, "%s: no entries", path);
     const size_t entries_end = s.find(']', p);
@@ -493,6 +520,10 @@ int cache_load(const char *path, const char *expect_device) {
             key >= kTuneKeys || id < 0 || id >= kVariantCount)
             return fail(WXPY_EINVAL, "%s: malformed entry", path);
         entries.emplace_back((int)key, (int)id);
+        long long lb = 0;
+        if (find_int(s, p, q, "launch_bound", &lb) && (lb < 0 || lb > 1))
+            return fail(WXPY_EINVAL, "%s: malformed entry", path);
+        entry_lb.push_back((int)lb);
         p = q;
     }
     // Optional batch shapes (written by this library since the batched launch).
@@ -568,7 +599,10 @@ int cache_load(const char *path, const char *expect_device) {
             q = r;
         }
     }
-    for (auto &kv : entries) g_tuned[kv.first].store(kv.second);
+    for (size_t i = 0; i < entries.size(); ++i) {
+        g_tuned[entries[i].first].store(entries[i].second);
+        g_tuned_launch_bound[entries[i].first].store(entry_lb[i]);
+    }
     if (have_batch) set_batch_shape(bs);
     for (auto &cv : vec) vecops_tuned_store(cv.first, &cv.second);
     for (auto &rc : red) reduce_tuned_store(rc.first, &rc.second);
@@ -629,11 +663,13 @@ int wxpy_tune_set(int tune_key, int variant_id) {
     if (variant_id < -1 || variant_id >= kVariantCount)
         return fail(WXPY_EINVAL, "bad variant id %d", variant_id);
     g_tuned[tune_key].store(variant_id);
+    g_tuned_launch_bound[tune_key].store(0);
     return WXPY_OK;
 }
 
 int wxpy_tune_clear(void) {
     for (auto &t : g_tuned) t.store(-1);
+    for (auto &t : g_tuned_launch_bound) t.store(0);
     for (int c = 0; c < WXPY_VEC_CLASSES; ++c) vecops_tuned_store(c, nullptr);
     for (int k = 0; k < 2; ++k) reduce_tuned_store(k, nullptr);
     return WXPY_OK;

@@ -140,3 +140,24 @@ print("traced ok")
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "traced ok" in r.stdout, r.stderr[-2000:]
+
+
+def test_launch_bound_cells_get_a_fixed_choice():
+    """n = 1024: every shape, the plain reference variant included, times at the
+    launch floor, so the search marks the cell launch-bound and stores the
+    first candidate within the tie band.  n = 2^26: the vector shapes beat the
+    plain variant by far more than the band, so the cell is not launch-bound."""
+    r = wx.wxpy_tune(1024, wx.TUNE_QUICK)
+    assert r["launch_bound"] == 1 and r["ties"] >= 2, r
+    assert r["reference_us"] <= r["best_us"] * 1.03 + 0.05
+    key = r["tune_key"]
+    assert wx.wxpy_tune_get(key) == r["best"]["id"]
+    big = wx.wxpy_tune(1 << 26, wx.TUNE_QUICK)
+    assert big["launch_bound"] == 0, big
+    assert big["reference_us"] > big["best_us"] * 1.03
+    # the chosen variant still reproduces the oracle at a ragged size of the cell
+    n = 1024 + 3
+    alpha, xh, yh, gx, gy, gw = _case(n)
+    wx.wxpy(alpha, gx.t, gy.t, gw.t)
+    ok, msg = bits_equal(gw.t, oracle.wxpy(alpha, xh, yh))
+    assert ok, msg

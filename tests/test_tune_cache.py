@@ -42,6 +42,20 @@ def test_load_without_device_check(tmp_path):
     assert wx.wxpy_tune_get(12 * 28 + 1) == 77
 
 
+def test_load_launch_bound_flag(tmp_path):
+    """Cells the search found launch-bound carry "launch_bound": 1 (optional;
+    0 when absent); any other value makes the file malformed."""
+    p = write(tmp_path / "lb.json", [{"key": 12 * 10, "variant": 240, "launch_bound": 1},
+                                     {"key": 12 * 24, "variant": 19920, "launch_bound": 0},
+                                     {"key": 12 * 25, "variant": 19696}])
+    wx.wxpy_tune_cache_load(p, check_device=False)
+    assert wx.wxpy_tune_get(12 * 10) == 240 and wx.wxpy_tune_get(12 * 25) == 19696
+    bad = write(tmp_path / "lb2.json", [{"key": 12 * 11, "variant": 240, "launch_bound": 2}])
+    with pytest.raises(wx.WxpyError):
+        wx.wxpy_tune_cache_load(bad, check_device=False)
+    assert wx.wxpy_tune_get(12 * 11) == -1
+
+
 @pytest.mark.parametrize("entries,fmt", [
     ([{"key": 3, "variant": 99999999}], "wxpy-tune-1"),
     ([{"key": -1, "variant": 5}], "wxpy-tune-1"),
