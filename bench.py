@@ -621,8 +621,10 @@ def write_jsonl(path, result):
 
 def tune_buckets(wx, args, torch):
     """Run wxpy_tune for every bucket of the sweep (n = 2^k) and both alias
-    groups the step times (distinct, and in place: w = x or w = y), or load
-    the cells from --tune-cache when that file exists; returns a summary."""
+    groups the step times (distinct, and in place: w = x or w = y), and for
+    the x = y and mixed-offset classes at the buckets of the sweep table's
+    class rows; or load the cells from --tune-cache when that file exists;
+    returns a summary."""
     t0 = time.perf_counter()
     if args.tune_cache and os.path.exists(args.tune_cache):
         wx.wxpy_tune_cache_load(args.tune_cache, check_device=True)
@@ -631,14 +633,19 @@ def tune_buckets(wx, args, torch):
     if args.no_tune:
         return {"source": "built-in default variant (tuning skipped)"}
     rows = []
-    for k in SWEEP_K:
-        for group, flags in (("distinct", 0), ("in_place", wx.binding.TUNE_WALIAS)):
-            r = wx.wxpy_tune(1 << k, flags)
-            rows.append({"k": k, "group": group, "variant": r["best"], "us": r["best_us"],
-                         "default_us": r["default_us"], "reference_us": r["reference_us"],
-                         "gbs": r["best_gbs"], "candidates": r["candidates"],
-                         "rejected": r["rejected"], "ties": r["ties"],
-                         "launch_bound": r["launch_bound"]})
+    # the step's classes at every bucket; the sweep table's x = y and
+    # mixed-offset classes at the buckets it measures
+    plan = [(k, g, f) for k in SWEEP_K
+            for g, f in (("distinct", 0), ("in_place", wx.binding.TUNE_WALIAS))]
+    plan += [(k, g, f) for k in (24, 26, 28)
+             for g, f in (("x=y", wx.binding.TUNE_XY), ("mixed", wx.binding.TUNE_ALIGN8))]
+    for k, group, flags in plan:
+        r = wx.wxpy_tune(1 << k, flags)
+        rows.append({"k": k, "group": group, "variant": r["best"], "us": r["best_us"],
+                     "default_us": r["default_us"], "reference_us": r["reference_us"],
+                     "gbs": r["best_gbs"], "candidates": r["candidates"],
+                     "rejected": r["rejected"], "ties": r["ties"],
+                     "launch_bound": r["launch_bound"]})
     torch.cuda.synchronize()
     if args.tune_cache:
         wx.wxpy_tune_cache_save(args.tune_cache)
@@ -756,7 +763,9 @@ def measure_config1(wx, lib, torch, dev, sh, stream, peak, reps=15, copies=16):
     independent (x, y, w) sets (16 x 24 MiB, together larger than L2), the L2
     flushed, then one call on each set back to back, per-call time = total /
     copies; also replayed from a CUDA graph of those calls.  L2-resident:
-    back-to-back calls on one set."""
+    back-to-back calls on one set.  For context, torch.add(x, y, out=w) -- an
+    elementwise kernel moving the same 24 bytes per element -- in the same
+    flushed forms."""
     from paper_1309_1894_gb300 import synth
     n = 1 << 20
     seed = synth.BASE_SEED + 1
@@ -797,7 +806,44 @@ def measure_config1(wx, lib, torch, dev, sh, stream, peak, reps=15, copies=16):
         e1.synchronize()
         tg.append(e0.elapsed_time(e1) / copies)
     ms_g = statistics.median(tg)
-    del g, sets, flush
+    # Context, not the product: PyTorch's own elementwise kernel moving the
+    # same 24 bytes per element (w = x + y in FP64) in the same two forms.
+    tbatch = [(a, b, c) for a, b, c in sets]
+
+    def torch_add():
+        for a, b, c in tbatch:
+            torch.add(a, b, out=c)
+    tt = []
+    for _ in range(reps):
+        flush.sum()
+        torch.cuda._sleep(1000000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch_add()
+        e1.record(stream)
+        e1.synchronize()
+        tt.append(e0.elapsed_time(e1) / copies)
+    ms_t = statistics.median(tt)
+    gt = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        torch_add()
+        cap.synchronize()
+        with torch.cuda.graph(gt, stream=cap):
+            torch_add()
+    tt = []
+    for _ in range(reps):
+        flush.sum()
+        torch.cuda._sleep(1000000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gt.replay()
+        e1.record(stream)
+        e1.synchronize()
+        tt.append(e0.elapsed_time(e1) / copies)
+    ms_tg = statistics.median(tt)
+    del g, gt, sets, tbatch, flush
     gbs = lambda ms: BYTES_PER_ELEM * n / (ms / 1e3) / 1e9
     v, src = lookup_ptr(wx, *batch[0][:1], *batch[0][2:5])
     return {"n": n, "alpha": alpha, "copies": copies, "reps": reps, "variant": v["id"],
@@ -805,6 +851,7 @@ def measure_config1(wx, lib, torch, dev, sh, stream, peak, reps=15, copies=16):
             "gbs_l2_flushed": gbs(ms_f), "us_l2_flushed": ms_f * 1e3,
             "gbs_l2_resident": gbs(ms_r), "us_l2_resident": ms_r * 1e3,
             "gbs_graph_flushed": gbs(ms_g), "us_graph_flushed": ms_g * 1e3,
+            "torch_add_us_flushed": ms_t * 1e3, "torch_add_us_graph_flushed": ms_tg * 1e3,
             "frac_of_peak_flushed": gbs(ms_f) / peak,
             "at_peak_us": BYTES_PER_ELEM * n / (peak * 1e9) * 1e6}
 

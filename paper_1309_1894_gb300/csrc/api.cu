@@ -12,6 +12,7 @@
 #include <unordered_map>
 
 #include "internal.h"
+#include "mixed_kernel.cuh"
 #include "trace.h"
 
 namespace wx {
@@ -213,7 +214,16 @@ int classify(int64_t n, const double *x, const double *y, const double *w, CallC
 
 Variant adjust_variant(const Variant &v, const CallClass &c) {
     Variant a = v;
-    a.vec_bytes = std::min(v.vec_bytes, c.align);
+    if (v.vec_bytes == 32 && c.align < 32) {
+        // Mixed alignment: 32-byte stores on w and per-input load widths
+        // (mixed_kernel.cuh), whose instances cover unroll 1..4, the
+        // non-coherent and coherent cache forms and offload 0 or 1.
+        a.unroll = std::min(v.unroll, 4);
+        if (a.cache == 0) a.cache = 1;
+        a.offload = std::min(v.offload, 1);
+    } else {
+        a.vec_bytes = std::min(v.vec_bytes, c.align);
+    }
     if (a.cache == 1 && (c.alias & (WXPY_ALIAS_WX | WXPY_ALIAS_WY))) a.cache = 2;
     return a;
 }
@@ -288,6 +298,11 @@ int split_resources(int device, SplitResources **out) {
     return WXPY_OK;
 }
 
+// Offset of p relative to w modulo 32 bytes: 0, 8, 16 or 24.
+int rel32(const void *p, const void *w) {
+    return (int)((((uintptr_t)p % 32u) + 32u - ((uintptr_t)w % 32u)) % 32u);
+}
+
 // One contiguous piece [x, x+n) with one kernel launch.
 int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, double alpha,
                  const double *x, const double *y, double *w, cudaStream_t s) {
@@ -298,8 +313,14 @@ int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, dou
     const int64_t head = std::min<int64_t>((vw - off) % vw, n);
     SingleArgs a{x, y, w, alpha, n, head, (n - head) / vw};
     const int u_idx = v.unroll == 1 ? 0 : v.unroll == 2 ? 1 : v.unroll == 4 ? 2 : 3;
+    const int rx = rel32(x, w), ry = rel32(y, w);
+    // 32-byte variants on pointers whose offsets disagree modulo 32 bytes run
+    // the mixed-alignment kernel (stores aligned on w, per-input load widths).
     const SingleEntry ent =
-        single_entry(vw, v.offload, u_idx, v.blocks_per_sm > 0 ? 1 : 0, v.cache, xy);
+        (vw == 4 && (rx | ry) != 0)
+            ? mixed_entry(mixed_width(rx), mixed_width(ry), std::min(u_idx, 2), v.cache, xy,
+                          v.offload)
+            : single_entry(vw, v.offload, u_idx, v.blocks_per_sm > 0 ? 1 : 0, v.cache, xy);
     // Instances that keep many registers live per thread have a smaller launch
     // bound; the block size is capped at it.
     const int threads = std::min(v.threads, ent.max_threads);
@@ -330,6 +351,12 @@ SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int 
         case 1 * 3 + 2: return SingleTable<1, 2>::get(u_idx, gs, cache, xy);
         default: return SingleTable<1, 0>::get(u_idx, gs, cache, xy);
     }
+}
+
+SingleEntry mixed_entry(int kx, int ky, int u_idx, int cache, int xy, int offload) {
+    const int c = cache == 2 ? 2 : 1;
+    return offload ? MixedTable<1>::get(kx, ky, u_idx, c, xy)
+                   : MixedTable<0>::get(kx, ky, u_idx, c, xy);
 }
 
 cudaError_t injected_launch_error() {

@@ -160,5 +160,7 @@ void reduce_tuned_store(int kind, const ReduceConfig *c);  // nullptr clears
 
 cudaError_t launch_reference(unsigned grid, unsigned tpb, const SingleArgs &a, cudaStream_t s);
 SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy);
+// The mixed-alignment instance (mixed_kernel.cuh) for input load widths kx, ky.
+SingleEntry mixed_entry(int kx, int ky, int u_idx, int cache, int xy, int offload);
 
 }  // namespace wx

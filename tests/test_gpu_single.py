@@ -226,6 +226,71 @@ def test_every_compiled_instance_forced(alias):
         g.check()
     assert count == 216
 
+MIXED_CASES = [(ox, oy, ow) for ox in (0, 8, 16, 24) for oy in (0, 8, 16, 24)
+               for ow in (0, 8, 24)]
+
+
+def test_every_mixed_instance_forced():
+    """The mixed-alignment kernel (32-byte variants on pointers whose offsets
+    disagree modulo 32 bytes): every pair of input load widths, reached through
+    x, y, w offsets whose differences are 0, 8, 16 and 24 bytes, with w's own
+    offset moving the head peel; unroll 1/2/4, the non-coherent and coherent
+    cache forms, fp64_offload 0/1, one-shot and grid-stride grids; at a ragged n
+    with several passes and a tail.  Bit for bit against the oracle, guards
+    untouched."""
+    enc = wx.wxpy_variant_encode
+    n = 3 * 4096 + 37
+    runs = 0
+    pairs = set()
+    for (ox, oy, ow) in MIXED_CASES:
+        rx, ry = (ox - ow) % 32, (oy - ow) % 32
+        if rx == 0 and ry == 0:
+            continue
+        if (rx, ry) in pairs and ow != 8:
+            continue  # each width pair with two different w offsets is enough
+        pairs.add((rx, ry))
+        alpha, (x, y, w), _, want, guards = make_case(n, 0, "none", 900 + ox + 3 * oy + 7 * ow,
+                                                      offs=(ox, oy, ow))
+        want_d = torch.from_numpy(want).cuda()
+        for u in (1, 2, 4):
+            for c in (1, 2):
+                for of in (0, 1):
+                    for bps in (0, 2):
+                        vid = enc(vec_bytes=32, unroll=u, threads=256, blocks_per_sm=bps,
+                                  cache=c, carveout=-1, streams=1, fp64_offload=of)
+                        w.fill_(7.0)
+                        wx.wxpy_run_variant(vid, alpha, x, y, w)
+                        torch.cuda.synchronize()
+                        assert dev_bits_equal(w, want_d), (ox, oy, ow, u, c, of, bps)
+                        runs += 1
+        for g in guards:
+            g.check()
+    assert len(pairs) == 15 and runs >= 15 * 24
+
+
+@pytest.mark.parametrize("alias,offs", [("x=y", (8, 8, 0)), ("x=y", (16, 16, 0)),
+                                        ("x=y", (0, 0, 24)), ("w=x", (8, 0, 8)),
+                                        ("w=x", (16, 8, 16)), ("w=y", (0, 24, 24)),
+                                        ("w=y", (8, 16, 16))])
+def test_mixed_kernel_aliasing(alias, offs):
+    """x == y offset from w, and in-place calls (w == x, w == y) whose other
+    input is offset from w: the mixed kernel under every unroll and cache form."""
+    enc = wx.wxpy_variant_encode
+    for n in (5, 4099, 70001):
+        alpha, (x, y, w), (xh, yh), want, guards = make_case(n, 0, alias, 31 + n, offs=offs)
+        for u in (1, 2, 4):
+            for c in (0, 1, 2):
+                vid = enc(vec_bytes=32, unroll=u, threads=256, blocks_per_sm=0,
+                          cache=c, carveout=-1, streams=1, fp64_offload=1)
+                restore(alias, x, y, xh, yh)
+                wx.wxpy_run_variant(vid, alpha, x, y, w)
+                torch.cuda.synchronize()
+                ok, msg = bits_equal(w, want)
+                assert ok, (alias, offs, n, u, c, msg)
+        for g in guards:
+            g.check()
+
+
 @pytest.mark.parametrize("alias", ALIASES)
 def test_tiny_sizes_exhaustive(alias):
     """n = 0..67 at every 8-byte offset, default lookup and reference variant."""
@@ -381,7 +446,14 @@ def test_lookup_reports_adjusted_variant():
     n = 1000
     _, (x, y, w), _, _, _ = make_case(n, 8, "none", 1, offs=(0, 8, 8))
     v, src = wx.wxpy_lookup(x, y, w)
-    assert src == 0 and v["vec_bytes"] == 8
+    # the default's 32-byte width on a mixed class: the mixed-alignment kernel
+    assert src == 0 and v["vec_bytes"] == 32 and v["unroll"] <= 4
+    wx.wxpy_set_variant(wx.wxpy_variant_encode(vec_bytes=16, unroll=8, threads=256,
+                                               blocks_per_sm=0, cache=0, carveout=-1,
+                                               streams=1, fp64_offload=2))
+    v, src = wx.wxpy_lookup(x, y, w)
+    assert src == 2 and v["vec_bytes"] == 8 and v["unroll"] == 8  # narrowed, not mixed
+    wx.wxpy_set_variant(-1)
     _, (x, y, w), _, _, _ = make_case(n, 0, "w=x", 1)
     v, src = wx.wxpy_lookup(x, y, w)
     assert v["cache"] != 1
