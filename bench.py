@@ -1165,7 +1165,10 @@ SERVE_RATES = (1e3, 5.62e3, 3.16e4, 1.78e5, 1e6)
 SERVE_BACKFILL_US = 5000
 
 
-def measure_served(seconds):
+SERVED_MODES = ("batched", "batched_backfill", "serial", "fused")
+
+
+def measure_served(seconds, modes=SERVED_MODES):
     """Poisson arrivals at five rates from 1e3 to 1e6 requests/s, n log-uniform in
     [2^8, 2^24], alpha ~ U(-2,2), a 16 GiB admission budget, each rate for
     ``seconds``: the continuous-batching server (per batch: one fill launch
@@ -1179,12 +1182,14 @@ def measure_served(seconds):
     from paper_1309_1894_gb300.server import Server, SERVE_BATCHED, SERVE_SERIAL, SERVE_FUSED
     from paper_1309_1894_gb300 import synth
     out = {"budget_gib": 16, "n_range": [1 << 8, 1 << 24], "seconds_per_rate": seconds,
-           "rates": list(SERVE_RATES), "backfill_aging_us": SERVE_BACKFILL_US,
-           "batched": [], "batched_backfill": [], "serial": [], "fused": []}
+           "rates": list(SERVE_RATES), "backfill_aging_us": SERVE_BACKFILL_US, "n_streams": 2}
     for name, mode, admission in (("batched", SERVE_BATCHED, 0),
                                   ("batched_backfill", SERVE_BATCHED, SERVE_BACKFILL_US),
                                   ("serial", SERVE_SERIAL, 0),
                                   ("fused", SERVE_FUSED, 0)):
+        if name not in modes:
+            continue
+        out[name] = []
         with Server(budget_bytes=16 << 30, max_slots=4096, n_streams=2, max_batch=1024,
                     max_queue=65536, mode=mode, admission_us=admission) as sv:
             for i, rate in enumerate(SERVE_RATES):
@@ -1261,6 +1266,10 @@ def main():
                     help="load the tuned cells from this file if it exists, else tune and save")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of Poisson load per rate for the served leg (0 skips it)")
+    ap.add_argument("--served-only", default="",
+                    help="run only the served leg, for these comma-separated modes (batched, "
+                         "batched_backfill, serial, fused) at --serve-seconds per rate, and "
+                         "print its record as one JSON line")
     ap.add_argument("--single", type=int, default=0,
                     help="profiling mode: only run wxpy() on n = SINGLE, --reps times")
     ap.add_argument("--reps", type=int, default=5)
@@ -1275,6 +1284,20 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.served_only:
+        modes = tuple(m.strip() for m in args.served_only.split(","))
+        bad = [m for m in modes if m not in SERVED_MODES]
+        if bad:
+            ap.error(f"unknown served modes {bad}")
+        rec = measure_served(args.serve_seconds, modes)
+        if args.extras:
+            d = os.path.dirname(args.extras)
+            if d:
+                os.makedirs(d, exist_ok=True)
+            with open(args.extras, "w") as f:
+                json.dump(rec, f, indent=1)
+        print(json.dumps(rec), flush=True)
+        return 0
     if args.single and args.vecop:
         return run_vecop(args)
     if args.single:

@@ -691,6 +691,10 @@ typedef struct wxpy_server_stats {
     double head_wait_full_s;  /* time it waited because the arena was too full */
     int64_t backfilled;       /* requests admitted ahead of a waiting head */
     int64_t reserved;
+    double max_launch_host_s; /* longest host time the scheduler spent queueing one
+                                 batch's work (tables, copies, launches) */
+    double max_batch_s;       /* longest time from queueing a batch to the scheduler
+                                 seeing it complete */
 } wxpy_server_stats;
 
 /* Allocates the arena (cudaMalloc of budget_bytes), per-stream staging, and

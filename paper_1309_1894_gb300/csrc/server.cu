@@ -40,6 +40,8 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -142,23 +144,32 @@ struct ServePlan {
     int32_t pad;
 };
 
-// A batch in flight on one stream, with its staging (pinned host) and device
-// tables: descriptors, the fill plan of the seeded requests, the tile list of
-// the segmented kernel and its status word.
+// A batch in flight on one stream.  Its tables live in one staging region,
+// pinned on the host and mirrored on the device, so that a batch's tables go
+// up in ONE copy: [status word | descriptors | seeds | fill plan | tiles of
+// the segmented kernel], each part 256-byte aligned.  The status word is
+// uploaded as zero with the tables and comes back, after the kernels, into a
+// separate pinned word.
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
+    std::chrono::steady_clock::time_point t_launch;  // when the batch was queued
+    double host_s = 0;                               // host time queueing it
+    int64_t count = 0, elems = 0;                    // its requests and elements
     std::vector<uint64_t> tickets;
     int64_t cap_segs = 0, cap_tiles = 0;
-    wxpy_desc *h_table = nullptr, *d_table = nullptr;
-    uint64_t *h_seeds = nullptr, *d_seeds = nullptr;
-    ServePlan *h_plan = nullptr, *d_plan = nullptr;
-    TileRec *h_tiles = nullptr, *d_tiles = nullptr;
-    unsigned *h_status = nullptr, *d_status = nullptr;
+    char *h_stage = nullptr, *d_stage = nullptr;
+    size_t off_table = 0, off_seeds = 0, off_plan = 0, off_tiles = 0, stage_bytes = 0;
+    unsigned *h_status = nullptr;  // the status word of the last batch, copied back
+    template <class T>
+    T *host(size_t off) const { return (T *)(h_stage + off); }
+    template <class T>
+    T *dev(size_t off) const { return (T *)(d_stage + off); }
 };
 
-// Elements per tile of the fill launch (one warp per tile).
+// Elements per tile of the fill launch (one warp per tile), for batches large
+// enough to fill the GPU with such tiles.
 constexpr int64_t kFillTile = 8192;
 
 // Largest s in [lo, count) with plan[s].first_tile <= t (tiles only grow
@@ -251,8 +262,9 @@ __global__ void __launch_bounds__(256) serve_fused_kernel(const wxpy_desc *table
 // The inputs step of a batch: for every seeded request, x and y from the
 // request's seed (streams (seed, 1) and (seed, 2), the values
 // wxpy_fill_uniform writes) stored into its resident buffers.  A warp takes a
-// tile of kFillTile elements; a lane writes four consecutive elements as
-// 32-byte vectors (tiles start at multiples of kFillTile in 256-byte-aligned
+// tile of the plan's length (kFillTile, or shorter for a small batch: a
+// multiple of 256); a lane writes four consecutive elements as 32-byte
+// vectors (tiles start at multiples of that length in 256-byte-aligned
 // buffers), the ragged end of a tile element by element.  Requests with
 // caller data have no tiles in the plan.  Reads nothing; 16 bytes written per
 // element.
@@ -267,8 +279,9 @@ __global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
     for (int64_t t = warp; t < ntiles; t += nwarps) {
         s = find_request(plan, count, t, s);
         const wxpy_desc d = table[s];
-        const int64_t begin = (t - plan[s].first_tile) * kFillTile;
-        const int64_t end = min(d.n, begin + kFillTile);
+        const ServePlan sp = plan[s];
+        const int64_t begin = (t - sp.first_tile) * sp.tile_len;
+        const int64_t end = min(d.n, begin + sp.tile_len);
         const uint64_t kx = stream_key_of(seeds[s], 1), ky = stream_key_of(seeds[s], 2);
         double *x = const_cast<double *>(d.x), *y = const_cast<double *>(d.y);
         const int64_t nvec = (end - begin) >> 2;
@@ -290,19 +303,32 @@ __global__ void __launch_bounds__(256) serve_fill_kernel(const wxpy_desc *table,
     }
 }
 
+// Tile length cap for a batch of `elems` elements: small batches are cut into
+// shorter tiles (down to 256 elements), so that their warps still spread over
+// every SM -- with the batched shape's 8192-element tiles, a lone request of
+// 65k elements would run on one block.  Batches of kTargetTiles x 8192
+// elements and more keep the shape's tiles.
+constexpr int64_t kTargetTiles = 4864;  // 152 SMs x 4 blocks x 8 warps
+int64_t tile_cap(int64_t elems) {
+    int64_t t = 8192;
+    while (t > 256 && elems / t < kTargetTiles) t >>= 1;
+    return t;
+}
+
 // Tile list of a batch for the segmented kernel: each request cut into tiles
-// of its size bucket's length (the batch shape, as in wxpy_batch), ordered
+// of its size bucket's length (the batch shape, as in wxpy_batch; at most
+// t_cap elements), ordered
 // longest first by power-of-two class of the tile length -- a stable counting
 // sort, linear in the tiles, so that the static round-robin over warps ends
 // on short tiles.  Returns the tile count; writes the tiles only when they
 // fit in `cap`.
-int64_t serve_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape, TileRec *out,
-                     int64_t cap) {
+int64_t serve_tiles(const wxpy_desc *t, int64_t count, const BatchShape &shape, int64_t t_cap,
+                     TileRec *out, int64_t cap) {
     int64_t per_class[64] = {0};
     auto tile_len = [&](int64_t n) {
         const int b = 63 - __builtin_clzll((unsigned long long)n);
         const int64_t T = shape.tile_elems[b] > 0 ? shape.tile_elems[b] : n;
-        return std::min<int64_t>(T, kMaxTileElems);
+        return std::min<int64_t>(std::min<int64_t>(T, t_cap), kMaxTileElems);
     };
     auto cls = [](int64_t len) { return 63 - __builtin_clzll((unsigned long long)len); };
     int64_t total = 0;
@@ -366,6 +392,7 @@ struct wxpy_server {
     int64_t submitted = 0, rejected = 0, completed = 0, failed = 0, max_queue = 0;
     int64_t batches = 0, launches = 0, elements_done = 0, requests_launched = 0;
     int64_t max_inflight = 0;  // most batches on the device at once
+    double max_launch_host = 0, max_batch = 0;  // seconds, see wxpy_server_stats
     int64_t backfilled = 0;
     double head_wait_frag = 0, head_wait_full = 0;  // seconds
     std::vector<double> latencies;
@@ -382,40 +409,41 @@ struct wxpy_server {
 namespace wx {
 namespace {
 
-void free_tiles(Slot &s) {
-    if (s.d_tiles) cudaFree(s.d_tiles);
-    if (s.h_tiles) cudaFreeHost(s.h_tiles);
-    s.d_tiles = nullptr;
-    s.h_tiles = nullptr;
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+void free_stage(Slot &s) {
+    if (s.d_stage) cudaFree(s.d_stage);
+    if (s.h_stage) cudaFreeHost(s.h_stage);
+    s.d_stage = s.h_stage = nullptr;
+    s.stage_bytes = 0;
     s.cap_tiles = 0;
 }
 
-// (Re)sizes the slot's tile list for `tiles` records; the slot must be idle.
-cudaError_t ensure_tiles(Slot &s, int64_t tiles) {
-    if (tiles <= s.cap_tiles) return cudaSuccess;
-    free_tiles(s);
-    const int64_t cap = std::max<int64_t>(tiles, 4096);
-    cudaError_t e = cudaMalloc(&s.d_tiles, sizeof(TileRec) * cap);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_tiles, sizeof(TileRec) * cap);
+// (Re)allocates the slot's staging region for `segs` requests and `tiles`
+// tile records; the slot must be idle.
+cudaError_t alloc_stage(Slot &s, int64_t segs, int64_t tiles) {
+    free_stage(s);
+    s.off_table = 256;
+    s.off_seeds = s.off_table + align256(sizeof(wxpy_desc) * segs);
+    s.off_plan = s.off_seeds + align256(sizeof(uint64_t) * segs);
+    s.off_tiles = s.off_plan + align256(sizeof(ServePlan) * segs);
+    const size_t bytes = s.off_tiles + sizeof(TileRec) * (size_t)tiles;
+    cudaError_t e = cudaMalloc(&s.d_stage, bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_stage, bytes);
     if (e != cudaSuccess) {
-        free_tiles(s);
+        free_stage(s);
         return e;
     }
-    s.cap_tiles = cap;
+    s.stage_bytes = bytes;
+    s.cap_segs = segs;
+    s.cap_tiles = tiles;
     return cudaSuccess;
 }
 
 void free_slot(Slot &s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.d_table) cudaFree(s.d_table);
-    if (s.d_seeds) cudaFree(s.d_seeds);
-    if (s.d_plan) cudaFree(s.d_plan);
-    if (s.d_status) cudaFree(s.d_status);
-    if (s.h_table) cudaFreeHost(s.h_table);
-    if (s.h_seeds) cudaFreeHost(s.h_seeds);
-    if (s.h_plan) cudaFreeHost(s.h_plan);
+    free_stage(s);
     if (s.h_status) cudaFreeHost(s.h_status);
-    free_tiles(s);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot{};
@@ -425,25 +453,34 @@ void free_slot(Slot &s) {
 cudaError_t init_slot(Slot &s, int64_t segs, int64_t tiles) {
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_table, sizeof(wxpy_desc) * segs);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_seeds, sizeof(uint64_t) * segs);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_plan, sizeof(ServePlan) * segs);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_table, sizeof(wxpy_desc) * segs);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_seeds, sizeof(uint64_t) * segs);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_plan, sizeof(ServePlan) * segs);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(s.d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) {
         *s.h_status = 0;
-        e = ensure_tiles(s, tiles);
+        e = alloc_stage(s, segs, std::max<int64_t>(tiles, 4096));
     }
-    s.cap_segs = segs;
     return e;
 }
 
 // Marks the requests of a finished (or failed) slot; caller holds the lock.
+// WXPY_SERVE_SLOW_MS=<ms>: a diagnostic; every batch whose host queueing or
+// queue-to-completion time exceeds that many milliseconds is reported on
+// stderr with its size.  Read once.
+double slow_batch_threshold_s() {
+    static const double v = [] {
+        const char *e = std::getenv("WXPY_SERVE_SLOW_MS");
+        return e && *e ? std::atof(e) * 1e-3 : -1.0;
+    }();
+    return v;
+}
+
 void retire_slot(wxpy_server *sv, Slot &s, Clock::time_point now, int error) {
+    const double batch_s = seconds(now - s.t_launch);
+    sv->max_batch = std::max(sv->max_batch, batch_s);
+    const double slow = slow_batch_threshold_s();
+    if (slow > 0 && (batch_s > slow || s.host_s > slow))
+        std::fprintf(stderr, "wxpy server: slow batch on stream %p: %lld requests, %lld elements, "
+                     "host %.3f ms, queue to completion %.3f ms\n", (void *)s.stream,
+                     (long long)s.count, (long long)s.elems, s.host_s * 1e3, batch_s * 1e3);
     // A set status word means the segmented kernel skipped a tile that did not
     // fit its descriptor: the batch's results are incomplete.
     if (!error && s.h_status && *s.h_status) error = kTileCheckFailed;
@@ -515,12 +552,20 @@ cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> 
     // Descriptors, and the plan of the generated inputs: the fill's tiles in
     // the batched mode, the fused kernel's (per-bucket tile length) in the
     // fused mode; caller-data requests get none.
-    int64_t nplan = 0;
+    wxpy_desc *h_table = s.host<wxpy_desc>(s.off_table);
+    uint64_t *h_seeds = s.host<uint64_t>(s.off_seeds);
+    ServePlan *h_plan = s.host<ServePlan>(s.off_plan);
+    int64_t nplan = 0, elems = 0, seeded = 0;
+    for (const Request *r : batch) {
+        elems += r->n;
+        if (r->src_kind < 0) seeded += r->n;
+    }
+    const int64_t fill_tile = std::min<int64_t>(kFillTile, tile_cap(seeded));
     for (int64_t i = 0; i < count; ++i) {
         const Request *r = batch[i];
-        s.h_table[i] = wxpy_desc{r->n, r->alpha, r->x, r->y, r->w};
-        s.h_seeds[i] = r->seed;
-        int64_t T = kFillTile;
+        h_table[i] = wxpy_desc{r->n, r->alpha, r->x, r->y, r->w};
+        h_seeds[i] = r->seed;
+        int64_t T = fill_tile;
         int ulog = 0;
         if (fused) {
             const int b = 63 - __builtin_clzll((unsigned long long)r->n);
@@ -528,37 +573,47 @@ cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> 
                                   kMaxTileElems);
             ulog = std::min<int>(2, std::max<int>(0, shape.unroll_log2[b]));
         }
-        s.h_plan[i] = ServePlan{nplan, T, ulog, 0};
+        h_plan[i] = ServePlan{nplan, T, ulog, 0};
         if (r->src_kind < 0) nplan += (r->n + T - 1) / T;
     }
     int64_t ntiles = 0;
     if (!fused) {
         // The tile list of step (b), before anything of this batch is queued:
-        // the slot is idle (its last batch completed), so a list too short
-        // for this batch can be resized here.
-        ntiles = serve_tiles(s.h_table, count, shape, s.h_tiles, s.cap_tiles);
+        // the slot is idle (its last batch completed), so a region too short
+        // for this batch can be reallocated here (the tables are rewritten).
+        ntiles = serve_tiles(h_table, count, shape, tile_cap(elems), s.host<TileRec>(s.off_tiles),
+                             s.cap_tiles);
         if (ntiles > s.cap_tiles) {
-            if ((e = ensure_tiles(s, ntiles + ntiles / 4)) != cudaSuccess) return e;
-            ntiles = serve_tiles(s.h_table, count, shape, s.h_tiles, s.cap_tiles);
+            std::vector<wxpy_desc> t(h_table, h_table + count);
+            std::vector<uint64_t> sd(h_seeds, h_seeds + count);
+            std::vector<ServePlan> pl(h_plan, h_plan + count);
+            if ((e = alloc_stage(s, s.cap_segs, ntiles + ntiles / 4)) != cudaSuccess) return e;
+            h_table = s.host<wxpy_desc>(s.off_table);
+            h_seeds = s.host<uint64_t>(s.off_seeds);
+            h_plan = s.host<ServePlan>(s.off_plan);
+            std::copy(t.begin(), t.end(), h_table);
+            std::copy(sd.begin(), sd.end(), h_seeds);
+            std::copy(pl.begin(), pl.end(), h_plan);
+            ntiles = serve_tiles(h_table, count, shape, tile_cap(elems),
+                                 s.host<TileRec>(s.off_tiles), s.cap_tiles);
         }
     }
-    e = cudaMemcpyAsync(s.d_table, s.h_table, sizeof(wxpy_desc) * count, cudaMemcpyHostToDevice,
-                        s.stream);
-    if (e == cudaSuccess && nplan > 0)
-        e = cudaMemcpyAsync(s.d_seeds, s.h_seeds, sizeof(uint64_t) * count,
-                            cudaMemcpyHostToDevice, s.stream);
-    if (e == cudaSuccess && nplan > 0)
-        e = cudaMemcpyAsync(s.d_plan, s.h_plan, sizeof(ServePlan) * count,
-                            cudaMemcpyHostToDevice, s.stream);
+    // One upload: status word (zero), descriptors, seeds, plan, and the tiles.
+    *s.host<unsigned>(0) = 0u;
+    const size_t up = fused ? s.off_tiles : s.off_tiles + sizeof(TileRec) * (size_t)ntiles;
+    e = cudaMemcpyAsync(s.d_stage, s.h_stage, up, cudaMemcpyHostToDevice, s.stream);
     if (e != cudaSuccess) return e;
+    const wxpy_desc *d_table = s.dev<wxpy_desc>(s.off_table);
+    const uint64_t *d_seeds = s.dev<uint64_t>(s.off_seeds);
+    const ServePlan *d_plan = s.dev<ServePlan>(s.off_plan);
     const int64_t wpb = 256 / 32;
     if (fused) {
         const unsigned grid = (unsigned)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)8 * sv->sm_count, (nplan + wpb - 1) / wpb));
         e = injected_launch_error();
         if (e != cudaSuccess) return e;
-        serve_fused_kernel<kServePM><<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan,
-                                                                 count, nplan);
+        serve_fused_kernel<kServePM><<<grid, 256, 0, s.stream>>>(d_table, d_seeds, d_plan, count,
+                                                                 nplan);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sv->launches += 1;
         return cudaEventRecord(s.done, s.stream);
@@ -571,21 +626,18 @@ cudaError_t launch_batch(wxpy_server *sv, Slot &s, const std::vector<Request *> 
             1, std::min<int64_t>((int64_t)8 * sv->sm_count, (nplan + wpb - 1) / wpb));
         e = injected_launch_error();
         if (e != cudaSuccess) return e;
-        serve_fill_kernel<<<grid, 256, 0, s.stream>>>(s.d_table, s.d_seeds, s.d_plan, count,
-                                                      nplan);
+        serve_fill_kernel<<<grid, 256, 0, s.stream>>>(d_table, d_seeds, d_plan, count, nplan);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sv->launches += 1;
     }
     // (b) one segmented launch over the batch: reads x, y, writes w; its
-    // status word starts at zero and comes back with the batch
-    e = cudaMemcpyAsync(s.d_tiles, s.h_tiles, sizeof(TileRec) * ntiles, cudaMemcpyHostToDevice,
-                        s.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_status, 0, sizeof(unsigned), s.stream);
-    if (e != cudaSuccess) return e;
-    e = launch_segmented(s.d_table, s.d_tiles, ntiles, s.d_status, shape, sv->sm_count, s.stream);
+    // status word (uploaded as zero) comes back with the batch
+    unsigned *d_status = s.dev<unsigned>(0);
+    e = launch_segmented(d_table, s.dev<TileRec>(s.off_tiles), ntiles, d_status, shape,
+                         sv->sm_count, s.stream);
     if (e != cudaSuccess) return e;
     sv->launches += 1;
-    e = cudaMemcpyAsync(s.h_status, s.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s.stream);
+    e = cudaMemcpyAsync(s.h_status, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s.stream);
     if (e != cudaSuccess) return e;
     return cudaEventRecord(s.done, s.stream);
 }
@@ -705,7 +757,18 @@ void scheduler(wxpy_server *sv) {
                 }
             }
             if (!batch.empty()) {
+                const Clock::time_point t0 = Clock::now();
+                s.t_launch = t0;
                 const cudaError_t e = launch_batch(sv, s, batch);
+                {
+                    const double dt = seconds(Clock::now() - t0);
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    sv->max_launch_host = std::max(sv->max_launch_host, dt);
+                    s.host_s = dt;
+                    s.count = (int64_t)batch.size();
+                    s.elems = 0;
+                    for (const Request *r : batch) s.elems += r->n;
+                }
                 progress = true;
                 if (e != cudaSuccess) {
                     cudaGetLastError();
@@ -926,6 +989,8 @@ int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
     out->elements_done = sv->elements_done;
     out->arena_used = sv->arena.used();
     out->max_inflight = sv->max_inflight;
+    out->max_launch_host_s = sv->max_launch_host;
+    out->max_batch_s = sv->max_batch;
     out->window_s = seconds(Clock::now() - sv->t_reset);
     out->p50_s = percentile(sv->latencies, 0.50);
     out->p99_s = percentile(sv->latencies, 0.99);
@@ -946,6 +1011,7 @@ int wxpy_server_get_stats(wxpy_server *sv, int reset, wxpy_server_stats *out) {
         sv->submitted = sv->rejected = sv->completed = sv->failed = 0;
         sv->batches = sv->launches = sv->elements_done = sv->requests_launched = 0;
         sv->max_inflight = 0;
+        sv->max_launch_host = sv->max_batch = 0;
         sv->max_queue = (int64_t)sv->queue.size();
         sv->latencies.clear();
         sv->t_reset = Clock::now();

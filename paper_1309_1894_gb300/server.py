@@ -27,7 +27,8 @@ class ServerStats(ctypes.Structure):
         "max_queue", "batches", "launches", "elements_done", "arena_used", "max_inflight")] + \
         [(f, ctypes.c_double) for f in ("mean_batch", "window_s", "p50_s", "p99_s", "mean_s",
                                         "max_s", "head_wait_frag_s", "head_wait_full_s")] + \
-        [("backfilled", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+        [("backfilled", ctypes.c_int64), ("reserved", ctypes.c_int64),
+         ("max_launch_host_s", ctypes.c_double), ("max_batch_s", ctypes.c_double)]
 
 
 class LoadgenConfig(ctypes.Structure):

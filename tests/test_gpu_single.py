@@ -381,6 +381,41 @@ def test_full_size_sampled(n):
     torch.cuda.empty_cache()
 
 
+def test_bench_dominant_call_compared_in_full():
+    """The benchmark's dominant call as it is timed: n = 2^28 + 3, start offset
+    8 bytes, in place (w == x), alpha / 2, the variant the search picks for that
+    cell -- every one of the 268,435,459 results compared with the oracle on
+    host inputs from the seeded generator, chunk by chunk."""
+    n = (1 << 28) + 3
+    seed = synth.BASE_SEED
+    alpha = synth.alpha_scalar(seed) * 0.5
+    wx.wxpy_tune(1 << 28, wx.TUNE_WALIAS | wx.TUNE_QUICK)
+    try:
+        buf = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+        ybuf = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+        # x and y 8 bytes past a 256-byte boundary, like the benchmark's 2^28 + 3 call
+        x, y = buf[1:], ybuf[1:]
+        wx.wxpy_fill_uniform(x, seed, synth.TAG_X)
+        wx.wxpy_fill_uniform(y, seed, synth.TAG_Y)
+        v, src = wx.wxpy_lookup(x, y, x)
+        assert src == 1
+        wx.wxpy(alpha, x, y, x)
+        torch.cuda.synchronize()
+        got = x.cpu().numpy()
+        del buf, ybuf, x, y
+        torch.cuda.empty_cache()
+        chunk = 1 << 24
+        for start in range(0, n, chunk):
+            m = min(chunk, n - start)
+            xh = synth.uniform_pm1(seed, synth.TAG_X, m, start=start)
+            yh = synth.uniform_pm1(seed, synth.TAG_Y, m, start=start)
+            want = oracle.wxpy(alpha, xh, yh)
+            ok, msg = bits_equal(torch.from_numpy(got[start:start + m]), want)
+            assert ok, (start, v, msg)
+    finally:
+        wx.wxpy_tune_clear()
+
+
 def test_large_split_streams_sampled():
     """n = 2^30 (8 GiB per vector) through the 8-stream split, sampled."""
     n = 1 << 30
