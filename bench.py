@@ -292,8 +292,19 @@ class CpuSample:
 
 
 def cpu_baseline_leg(seconds: float):
-    """The repo arm's cpu_baseline: the CPU sample single-threaded for about
-    ``seconds``, then on all host cores for a third of that."""
+    """The repo arm's cpu_baseline, measured in a fresh process (no CUDA
+    context, no torch, none of the GPU legs' host memory), like the reference
+    arm: ``bench.py --cpu-sample SECONDS`` prints the record as one line."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(seconds)],
+                       capture_output=True, text=True, timeout=max(600.0, 20 * seconds))
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_sample_record(seconds: float):
+    """The CPU sample single-threaded for about ``seconds``, then on all host
+    cores for a third of that."""
     one = CpuSample(1)
     one.one_pass()  # warm-up pass: first touch of the host pages
     rate1, passes, dt = one.timed(seconds=seconds)
@@ -1266,6 +1277,9 @@ def main():
                     help="load the tuned cells from this file if it exists, else tune and save")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of Poisson load per rate for the served leg (0 skips it)")
+    ap.add_argument("--cpu-sample", type=float, default=0.0,
+                    help="only time the CPU sample (the oracle) for this many seconds and print "
+                         "the cpu_baseline record (the repo arm runs this in a fresh process)")
     ap.add_argument("--served-only", default="",
                     help="run only the served leg, for these comma-separated modes (batched, "
                          "batched_backfill, serial, fused) at --serve-seconds per rate, and "
@@ -1284,6 +1298,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_sample > 0:
+        print(json.dumps(cpu_sample_record(args.cpu_sample)), flush=True)
+        return 0
     if args.served_only:
         modes = tuple(m.strip() for m in args.served_only.split(","))
         bad = [m for m in modes if m not in SERVED_MODES]

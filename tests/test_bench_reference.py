@@ -32,3 +32,17 @@ def test_reference_arm_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_sample_record_matches_the_reference_arm():
+    """The repo arm's cpu_baseline comes from `bench.py --cpu-sample S` in a
+    fresh process: the same named sample and oracle call as the reference arm."""
+    r = subprocess.run([sys.executable, "bench.py", "--cpu-sample", "0.3"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    assert d["sample"].startswith(bench.CPU_SAMPLE)
+    assert d["all_cores"]["cores"] >= 1 and d["all_cores"]["value"] > 0
