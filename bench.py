@@ -869,12 +869,13 @@ def measure_config1(wx, lib, torch, dev, sh, stream, peak, reps=15, copies=16):
 
 def measure_offload(wx, lib, torch, x, y, w, alpha, sh, stream, peak, tuned, reps=20):
     """The tuned n = 2^28 variant with each FP64-offload setting: every sum on
-    the FP64 pipeline (0), half (1) or all (2) in the integer pipeline.  On
-    GB300 the FP64 pipeline caps two FP64 instructions per element near
-    6.2 TB/s; moving half the sums to the integer pipeline lifts that ceiling."""
+    the FP64 pipeline (0), half (1) or all (2) in the integer pipeline, or
+    every product in the integer pipelines (3).  On GB300 the FP64 pipeline
+    caps two FP64 instructions per element near 6.2 TB/s; moving half the sums
+    or every product off it lifts that ceiling."""
     n = 1 << DOMINANT_K
     out = []
-    for of in (0, 1, 2):
+    for of in (0, 1, 2, 3):
         fields = {k: v for k, v in tuned.items() if k != "id"}
         fields["fp64_offload"] = of
         vid = wx.wxpy_variant_encode(**fields)

@@ -130,8 +130,11 @@ typedef struct wxpy_variant_info {
     int32_t fp64_offload;  /* 0: both roundings on the FP64 pipeline; 1: the sum
                               of every other element of a pass, 2: every sum,
                               computed as an exactly rounded binary64 addition in
-                              the integer pipeline (same bits; the FP64 pipeline
-                              is the scarce unit on GB300) */
+                              the integer pipeline; 3: every product computed as
+                              an exactly rounded binary64 multiplication in the
+                              integer pipelines, the sums on the FP64 pipeline
+                              (same bits; the FP64 pipeline is the scarce unit on
+                              GB300) */
 } wxpy_variant_info;
 
 /* Number of variants in the space (vec_bytes x unroll x threads x grid mode x

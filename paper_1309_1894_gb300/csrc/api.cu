@@ -132,7 +132,7 @@ bool decode_variant(int id, Variant *v) {
     const int th = r % 4; r /= 4;
     const int un = r % 4; r /= 4;
     const int vb = r % 3; r /= 3;
-    const int of = r;  // < 3
+    const int of = r;  // < 4
     *v = Variant{kVecBytes[vb], kUnroll[un], kThreads[th], kBlocksPerSm[gr],
                  kCache[ca], kCarveout[co], kStreams[st], kOffload[of]};
     return true;
@@ -217,10 +217,11 @@ Variant adjust_variant(const Variant &v, const CallClass &c) {
     if (v.vec_bytes == 32 && c.align < 32) {
         // Mixed alignment: 32-byte stores on w and per-input load widths
         // (mixed_kernel.cuh), whose instances cover unroll 1..4, the
-        // non-coherent and coherent cache forms and offload 0 or 1.
+        // non-coherent and coherent cache forms and offload 0, 1 and 3
+        // (2 runs as 1).
         a.unroll = std::min(v.unroll, 4);
         if (a.cache == 0) a.cache = 1;
-        a.offload = std::min(v.offload, 1);
+        if (a.offload == 2) a.offload = 1;
     } else {
         a.vec_bytes = std::min(v.vec_bytes, c.align);
     }
@@ -311,7 +312,9 @@ int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, dou
     const int64_t vb = v.vec_bytes;
     const int64_t off = (int64_t)(((uintptr_t)w % (uintptr_t)vb) / 8);
     const int64_t head = std::min<int64_t>((vw - off) % vw, n);
-    SingleArgs a{x, y, w, alpha, n, head, (n - head) / vw};
+    uint64_t ab;
+    std::memcpy(&ab, &alpha, 8);
+    SingleArgs a{x, y, w, alpha, n, head, (n - head) / vw, mul_coef_of(ab)};
     const int u_idx = v.unroll == 1 ? 0 : v.unroll == 2 ? 1 : v.unroll == 4 ? 2 : 3;
     const int rx = rel32(x, w), ry = rel32(y, w);
     // 32-byte variants on pointers whose offsets disagree modulo 32 bytes run
@@ -340,23 +343,27 @@ int launch_piece(const Variant &v, const DeviceProps &dp, int xy, int64_t n, dou
 }  // namespace
 
 SingleEntry single_entry(int vw, int offload, int u_idx, int gs, int cache, int xy) {
-    switch (vw * 3 + offload) {
-        case 4 * 3 + 0: return SingleTable<4, 0>::get(u_idx, gs, cache, xy);
-        case 4 * 3 + 1: return SingleTable<4, 1>::get(u_idx, gs, cache, xy);
-        case 4 * 3 + 2: return SingleTable<4, 2>::get(u_idx, gs, cache, xy);
-        case 2 * 3 + 0: return SingleTable<2, 0>::get(u_idx, gs, cache, xy);
-        case 2 * 3 + 1: return SingleTable<2, 1>::get(u_idx, gs, cache, xy);
-        case 2 * 3 + 2: return SingleTable<2, 2>::get(u_idx, gs, cache, xy);
-        case 1 * 3 + 1: return SingleTable<1, 1>::get(u_idx, gs, cache, xy);
-        case 1 * 3 + 2: return SingleTable<1, 2>::get(u_idx, gs, cache, xy);
+    switch (vw * 4 + offload) {
+        case 4 * 4 + 0: return SingleTable<4, 0>::get(u_idx, gs, cache, xy);
+        case 4 * 4 + 1: return SingleTable<4, 1>::get(u_idx, gs, cache, xy);
+        case 4 * 4 + 2: return SingleTable<4, 2>::get(u_idx, gs, cache, xy);
+        case 4 * 4 + 3: return SingleTable<4, 3>::get(u_idx, gs, cache, xy);
+        case 2 * 4 + 0: return SingleTable<2, 0>::get(u_idx, gs, cache, xy);
+        case 2 * 4 + 1: return SingleTable<2, 1>::get(u_idx, gs, cache, xy);
+        case 2 * 4 + 2: return SingleTable<2, 2>::get(u_idx, gs, cache, xy);
+        case 2 * 4 + 3: return SingleTable<2, 3>::get(u_idx, gs, cache, xy);
+        case 1 * 4 + 1: return SingleTable<1, 1>::get(u_idx, gs, cache, xy);
+        case 1 * 4 + 2: return SingleTable<1, 2>::get(u_idx, gs, cache, xy);
+        case 1 * 4 + 3: return SingleTable<1, 3>::get(u_idx, gs, cache, xy);
         default: return SingleTable<1, 0>::get(u_idx, gs, cache, xy);
     }
 }
 
 SingleEntry mixed_entry(int kx, int ky, int u_idx, int cache, int xy, int offload) {
     const int c = cache == 2 ? 2 : 1;
-    return offload ? MixedTable<1>::get(kx, ky, u_idx, c, xy)
-                   : MixedTable<0>::get(kx, ky, u_idx, c, xy);
+    return offload == 3   ? MixedTable<3>::get(kx, ky, u_idx, c, xy)
+           : offload != 0 ? MixedTable<1>::get(kx, ky, u_idx, c, xy)
+                          : MixedTable<0>::get(kx, ky, u_idx, c, xy);
 }
 
 cudaError_t injected_launch_error() {

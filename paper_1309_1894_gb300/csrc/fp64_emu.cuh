@@ -32,6 +32,8 @@
 
 #include <cstdint>
 
+#include "fp64_mul.cuh"
+
 namespace wx {
 
 // The hardware sum for the rare operands the integer path leaves out, on bit
@@ -110,11 +112,33 @@ __device__ __forceinline__ double add_rn_int(double a, double b) {
 template <int VW, int EMU>
 __device__ __forceinline__ void wxpy_vec_emu(double alpha, const double (&x)[VW],
                                              const double (&y)[VW], double (&w)[VW], int base) {
+    static_assert(EMU >= 0 && EMU <= 2, "the product offload needs the coefficient split");
 #pragma unroll
     for (int k = 0; k < VW; ++k) {
         const double p = __dmul_rn(alpha, x[k]);
         const bool emu = EMU == 2 || (EMU == 1 && ((base + k) & 1));
         w[k] = emu ? add_rn_int(p, y[k]) : __dadd_rn(p, y[k]);
+    }
+}
+
+// The same with alpha's split `ca` at hand: EMU == 3 computes every product
+// RN(alpha*x) in the integer pipelines (fp64_mul.cuh; operands it leaves out
+// take the hardware multiply, out of line) and every sum on the FP64
+// pipeline, which then carries one instruction per element.
+template <int VW, int EMU>
+__device__ __forceinline__ void wxpy_vec_emu(double alpha, const MulCoef &ca, const double (&x)[VW],
+                                             const double (&y)[VW], double (&w)[VW], int base) {
+    if constexpr (EMU == 3) {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const uint64_t xb = (uint64_t)__double_as_longlong(x[k]);
+            bool slow = false;
+            uint64_t pb = mul_rn_core(ca, xb, slow);
+            if (slow) pb = mul_rn_hw_bits((uint64_t)__double_as_longlong(alpha), xb);  // out of line
+            w[k] = __dadd_rn(__longlong_as_double((long long)pb), y[k]);
+        }
+    } else {
+        wxpy_vec_emu<VW, EMU>(alpha, x, y, w, base);
     }
 }
 

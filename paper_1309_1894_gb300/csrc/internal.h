@@ -33,7 +33,7 @@ const DeviceProps *current_device(int *status);
 // ---- the variant space ----
 struct Variant {
     int vec_bytes, unroll, threads, blocks_per_sm, cache, carveout, streams;
-    int offload = 0;  // sums in the integer pipeline: 0 none, 1 half, 2 all
+    int offload = 0;  // integer pipeline: 0 nothing, 1 half the sums, 2 all sums, 3 all products
 };
 constexpr int kVecBytes[3] = {8, 16, 32};
 constexpr int kUnroll[4] = {1, 2, 4, 8};
@@ -42,9 +42,9 @@ constexpr int kBlocksPerSm[5] = {0, 1, 2, 4, 8};
 constexpr int kCache[3] = {0, 1, 2};
 constexpr int kCarveout[4] = {-1, 0, 50, 100};
 constexpr int kStreams[4] = {1, 2, 4, 8};
-constexpr int kOffload[3] = {0, 1, 2};
+constexpr int kOffload[4] = {0, 1, 2, 3};
 constexpr int kVariantsPerOffload = 3 * 4 * 4 * 5 * 3 * 4 * 4;
-constexpr int kVariantCount = kVariantsPerOffload * 3;
+constexpr int kVariantCount = kVariantsPerOffload * 4;
 
 bool decode_variant(int id, Variant *v);
 int encode_variant(const Variant &v);  // -1 if a field is out of the space

@@ -22,7 +22,8 @@
 //
 // Arithmetic as in the family (paper Sec. 3, Fig. 1, vecwxpy read as PETSc
 // VecWXPY): w = RN(RN(alpha*x) + y), never fused; EMU = 1 moves the sums of
-// odd element positions to the integer pipeline (fp64_emu.cuh).
+// odd element positions to the integer pipeline (fp64_emu.cuh), EMU = 3 every
+// product (fp64_mul.cuh).
 #pragma once
 
 #include "single_kernel.cuh"
@@ -63,8 +64,8 @@ __device__ __forceinline__ void mixed_pass(const SingleArgs &a, int64_t c0, int6
     for (int u = 0; u < U; ++u) {
         const int64_t c = c0 + u * tpb;
         if (c < a.nchunks) {
-            if constexpr (XY) wxpy_vec_emu<4, EMU>(a.alpha, xv[u], xv[u], wv[u], 0);
-            else wxpy_vec_emu<4, EMU>(a.alpha, xv[u], yv[u], wv[u], 0);
+            if constexpr (XY) wxpy_vec_emu<4, EMU>(a.alpha, a.ca, xv[u], xv[u], wv[u], 0);
+            else wxpy_vec_emu<4, EMU>(a.alpha, a.ca, xv[u], yv[u], wv[u], 0);
             st_vec<4, CACHE>(wb + 4 * c, wv[u]);
         }
     }

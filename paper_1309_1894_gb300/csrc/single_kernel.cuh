@@ -10,6 +10,8 @@
 //   CACHE  0: ld/st.global; 1: ld.global.nc.L1::no_allocate + st.global.cs;
 //          2: ld/st.global.cs (evict-first, coherent; used under aliasing)
 //   XY     x == y: y is not loaded and w = RN(RN(alpha*x) + x)
+//   EMU    which roundings run in the integer pipelines instead of FP64
+//          instructions: 0 none, 1 half the sums, 2 every sum, 3 every product
 // Threads per block and the grid size are launch parameters, not template
 // parameters.
 //
@@ -26,6 +28,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "fp64_mul.cuh"
+
 namespace wx {
 
 struct SingleArgs {
@@ -36,6 +40,7 @@ struct SingleArgs {
     int64_t n;         // total elements
     int64_t head;      // scalar elements before the vector body (< VW)
     int64_t nchunks;   // vector body: chunks of VW elements starting at `head`
+    MulCoef ca;        // alpha split for the integer-pipeline product (EMU == 3)
 };
 
 template <int VW, int CACHE>
@@ -110,9 +115,10 @@ __device__ __forceinline__ void wxpy_vec(double alpha, const double (&x)[VW],
 namespace wx {
 
 // One pass of one thread: chunks c0, c0 + tpb, ..., c0 + (U-1)*tpb.  EMU
-// selects which sums run in the integer pipeline (fp64_emu.cuh): none, the
-// odd positions of the pass, or all; the choice depends only on the position,
-// so it is the same for every lane of a warp.
+// selects which operations run in the integer pipelines (fp64_emu.cuh): 0
+// none; 1 the sums of odd positions of the pass; 2 every sum; 3 every
+// product (fp64_mul.cuh), the sums on the FP64 pipeline.  The choice depends
+// only on the position, so it is the same for every lane of a warp.
 template <int VW, int U, int CACHE, bool XY, int EMU>
 __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64_t tpb) {
     const double *xb = a.x + a.head;
@@ -128,8 +134,8 @@ __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], xv[u], wv[u], u * VW);
-            else wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], yv[u], wv[u], u * VW);
+            if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, a.ca, xv[u], xv[u], wv[u], u * VW);
+            else wxpy_vec_emu<VW, EMU>(a.alpha, a.ca, xv[u], yv[u], wv[u], u * VW);
             st_vec<VW, CACHE>(wb + (c0 + u * tpb) * VW, wv[u]);
         }
     } else {
@@ -145,8 +151,8 @@ __device__ __forceinline__ void wxpy_pass(const SingleArgs &a, int64_t c0, int64
         for (int u = 0; u < U; ++u) {
             const int64_t c = c0 + u * tpb;
             if (c < a.nchunks) {
-                if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], xv[u], wv[u], u * VW);
-                else wxpy_vec_emu<VW, EMU>(a.alpha, xv[u], yv[u], wv[u], u * VW);
+                if constexpr (XY) wxpy_vec_emu<VW, EMU>(a.alpha, a.ca, xv[u], xv[u], wv[u], u * VW);
+                else wxpy_vec_emu<VW, EMU>(a.alpha, a.ca, xv[u], yv[u], wv[u], u * VW);
                 st_vec<VW, CACHE>(wb + c * VW, wv[u]);
             }
         }
@@ -185,7 +191,8 @@ __device__ __forceinline__ void wxpy_edges(const SingleArgs &a, int64_t vw) {
 template <int VW, int U, int GS, bool XY, int EMU>
 constexpr int max_threads() {
     constexpr int regs =
-        2 * U * VW * (XY ? 1 : 2) + 6 * U + 20 + (GS ? 16 : 0) + (EMU ? 24 : 0);
+        2 * U * VW * (XY ? 1 : 2) + 6 * U + 20 + (GS ? 16 : 0) + (EMU ? 24 : 0) +
+        (EMU == 3 ? 8 : 0);
     return regs <= 64 ? 1024 : (regs <= 128 ? 512 : 256);
 }
 

@@ -46,10 +46,14 @@ def test_strerror(lib):
 
 def test_variant_space_roundtrip(lib):
     count = wx.wxpy_variant_count()
-    assert count == 3 * 4 * 4 * 5 * 3 * 4 * 4 * 3
-    # ids without the FP64 offload knob keep their meaning (offload is the top digit)
-    assert wx.wxpy_variant_describe(count // 3 - 1)["fp64_offload"] == 0
-    assert wx.wxpy_variant_describe(count // 3)["fp64_offload"] == 1
+    per = 3 * 4 * 4 * 5 * 3 * 4 * 4
+    assert count == per * 4
+    # ids without the FP64 offload knob keep their meaning (offload is the top digit),
+    # and so do those of the earlier offload values 1 and 2
+    assert wx.wxpy_variant_describe(per - 1)["fp64_offload"] == 0
+    assert wx.wxpy_variant_describe(per)["fp64_offload"] == 1
+    assert wx.wxpy_variant_describe(3 * per - 1)["fp64_offload"] == 2
+    assert wx.wxpy_variant_describe(3 * per)["fp64_offload"] == 3
     seen = set()
     for vid in range(0, count, 7):
         d = wx.wxpy_variant_describe(vid)

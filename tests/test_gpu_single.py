@@ -87,7 +87,7 @@ def offload_variants():
     enc = wx.wxpy_variant_encode
     return [enc(vec_bytes=vb, unroll=u, threads=128, blocks_per_sm=0, cache=2, carveout=-1,
                 streams=1, fp64_offload=of)
-            for of in (1, 2) for vb in (8, 16, 32) for u in (1, 4)]
+            for of in (1, 2, 3) for vb in (8, 16, 32) for u in (1, 4)]
 
 
 def _special_pairs():
@@ -119,13 +119,22 @@ def _special_pairs():
 
 def test_integer_pipeline_sum_is_exact():
     """fp64_offload variants give the oracle's bits (NaN by class) on inputs
-    chosen to hit every branch of the integer-pipeline adder."""
+    chosen to hit every branch of the integer-pipeline adder (offload 1, 2)
+    and the integer-pipeline product (offload 3: alpha = 1 and random alphas
+    times special and wide-exponent x)."""
     import pins
     xh, yh = _special_pairs()
     cases = [(1.0, xh, yh)]
     for seed in (1, 2):
         a, x, y = pins.random_cases(synth.BASE_SEED + 300 + seed, 20000)
         cases.append((a, x, y))
+    # the product's branches: alphas whose products with x run subnormal,
+    # overflow, round to the next binade, or are not normal themselves
+    _, xw, yw = pins.random_cases(synth.BASE_SEED + 303, 20000)
+    for alpha in (-0.75, 2.0 ** -600, 2.0 ** 600, 5e-324, -3.0, 1.0 + 2.0 ** -52, 1.5 - 2.0 ** -53):
+        cases.append((alpha, xh, yh))
+        cases.append((alpha, np.ldexp(xw, 400), yw))
+        cases.append((alpha, np.ldexp(xw, -400), yw))
     for alpha, x, y in cases:
         want = oracle.wxpy(alpha, x, y)
         xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
@@ -202,7 +211,7 @@ def test_every_variant_family_member(alias, off):
 def test_every_compiled_instance_forced(alias):
     """Every compiled kernel instance, forced through wxpy_run_variant on
     32-byte co-aligned pointers (so nothing narrows the vector width): vector
-    width x unroll x grid mode x cache policy x fp64_offload, with distinct x
+    width x unroll x grid mode x cache policy x fp64_offload (0..3), with distinct x
     and y or x == y (the template's x == y argument), at a ragged n that has a
     head-free body, several unrolled passes and a tail."""
     enc = wx.wxpy_variant_encode
@@ -213,7 +222,7 @@ def test_every_compiled_instance_forced(alias):
         for u in (1, 2, 4, 8):
             for bps in (0, 2):  # one-shot grid, grid-stride
                 for c in (0, 1, 2):
-                    for of in (0, 1, 2):
+                    for of in (0, 1, 2, 3):
                         vid = enc(vec_bytes=vb, unroll=u, threads=256, blocks_per_sm=bps,
                                   cache=c, carveout=-1, streams=1, fp64_offload=of)
                         w.fill_(7.0)
@@ -224,7 +233,7 @@ def test_every_compiled_instance_forced(alias):
                         count += 1
     for g in guards:
         g.check()
-    assert count == 216
+    assert count == 288
 
 MIXED_CASES = [(ox, oy, ow) for ox in (0, 8, 16, 24) for oy in (0, 8, 16, 24)
                for ow in (0, 8, 24)]
@@ -235,7 +244,7 @@ def test_every_mixed_instance_forced():
     disagree modulo 32 bytes): every pair of input load widths, reached through
     x, y, w offsets whose differences are 0, 8, 16 and 24 bytes, with w's own
     offset moving the head peel; unroll 1/2/4, the non-coherent and coherent
-    cache forms, fp64_offload 0/1, one-shot and grid-stride grids; at a ragged n
+    cache forms, fp64_offload 0/1/3, one-shot and grid-stride grids; at a ragged n
     with several passes and a tail.  Bit for bit against the oracle, guards
     untouched."""
     enc = wx.wxpy_variant_encode
@@ -254,7 +263,7 @@ def test_every_mixed_instance_forced():
         want_d = torch.from_numpy(want).cuda()
         for u in (1, 2, 4):
             for c in (1, 2):
-                for of in (0, 1):
+                for of in (0, 1, 3):
                     for bps in (0, 2):
                         vid = enc(vec_bytes=32, unroll=u, threads=256, blocks_per_sm=bps,
                                   cache=c, carveout=-1, streams=1, fp64_offload=of)
@@ -265,7 +274,7 @@ def test_every_mixed_instance_forced():
                         runs += 1
         for g in guards:
             g.check()
-    assert len(pairs) == 15 and runs >= 15 * 24
+    assert len(pairs) == 15 and runs >= 15 * 36
 
 
 @pytest.mark.parametrize("alias,offs", [("x=y", (8, 8, 0)), ("x=y", (16, 16, 0)),
