@@ -1263,7 +1263,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--jsonl", default=None,
                     help="also append one JSON line per measured case to this file")
     ap.add_argument("--extras", default=EXTRAS_DEFAULT,

@@ -193,8 +193,11 @@ int wxpy_host(int64_t n, double alpha, const double *hx, const double *hy, doubl
  * pipeline slots (1..8; default 3) and strategy of later wxpy_host() calls.
  * direct = 1: when all three buffers are mapped pinned memory (the runtime
  * gives them device addresses), the kernel reads x, y and writes w across the
- * host link itself -- no staging, both link directions at once; otherwise
- * (direct = 0, or unmapped memory) the staged pipeline above. */
+ * host link itself -- no staging, both link directions at once -- with one
+ * fixed member of the family chosen for the link (16-byte accesses, a
+ * grid-stride grid of four blocks per SM, integer-pipeline products), since
+ * the link bounds it; otherwise (direct = 0, or unmapped memory) the staged
+ * pipeline above, whose kernels use the tuned cells. */
 int wxpy_host_config(int64_t chunk_elems, int slots, int direct);
 
 /* Programmatic dependent launch of the single-call kernels (wxpy, wxpy_host's
