@@ -597,8 +597,9 @@ typedef struct wxpy_batch_tune_result {
     int32_t threads;
     int32_t candidates;      /* batched launches run */
     int32_t rejected;        /* candidates whose output differed from the reference */
-    int32_t fp64_offload;    /* chosen: 0 every sum on the FP64 pipeline, 1 half of
-                                them in the integer pipeline (see wxpy_variant_info) */
+    int32_t fp64_offload;    /* chosen: 0 every operation on the FP64 pipeline, 1 half
+                                of the sums, 3 every product in the integer pipelines
+                                (see wxpy_variant_info) */
     int32_t reserved;
 } wxpy_batch_tune_result;
 
@@ -607,7 +608,8 @@ typedef struct wxpy_batch_tune_result {
  * by running the plain reference variant on every segment, then runs the
  * batched launch with every (tile length, unroll) candidate, rejects any
  * whose output differs by a bit, and keeps the fastest (median time) for b.
- * Finally picks blocks per SM on a mixed batch.  The results replace the
+ * Finally picks blocks per SM and fp64_offload (0, 1 or 3) on a mixed batch.
+ * The results replace the
  * process's batch shape table, used by later plans.  Synchronous; allocates
  * and frees its own scratch.  flags: WXPY_TUNE_QUICK narrows the search. */
 int wxpy_batch_tune(int bucket_min, int bucket_max, unsigned flags,
@@ -621,8 +623,9 @@ int wxpy_batch_shape_set(int bucket, int tile_elems, int unroll);
 int wxpy_batch_shape_reset(void);
 
 /* Whole-launch knobs of the batched launch (and of the server's batches):
- * grid = blocks_per_sm (1..32) * sm_count, and fp64_offload 0 or 1 (half of the
- * sums in the integer pipeline, as for wxpy_variant_info).  Host only. */
+ * grid = blocks_per_sm (1..32) * sm_count, and fp64_offload 0, 1 (half of the
+ * sums in the integer pipeline) or 3 (every product in the integer pipelines),
+ * as for wxpy_variant_info.  Host only. */
 int wxpy_batch_launch_get(int *blocks_per_sm, int *fp64_offload);
 int wxpy_batch_launch_set(int blocks_per_sm, int fp64_offload);
 

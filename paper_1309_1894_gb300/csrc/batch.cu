@@ -37,7 +37,8 @@ struct SegParams {
     unsigned *status;  // bit 0: a tile exceeded its descriptor's n
 };
 
-// EMU: sums in the integer pipeline (0 none, 1 half), chosen per launch.
+// EMU: the integer-pipeline share (0 none, 1 half the sums, 3 every product),
+// chosen per launch.
 template <int EMU>
 __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
     const int lane = threadIdx.x & 31;
@@ -57,12 +58,15 @@ __global__ void __launch_bounds__(256, 2) wxpy_seg_kernel(const SegParams p) {
 }
 
 static const void *seg_kernel_fn(int offload) {
-    return offload ? (const void *)&wxpy_seg_kernel<1> : (const void *)&wxpy_seg_kernel<0>;
+    return offload == 3   ? (const void *)&wxpy_seg_kernel<3>
+           : offload != 0 ? (const void *)&wxpy_seg_kernel<1>
+                          : (const void *)&wxpy_seg_kernel<0>;
 }
 
 static cudaError_t seg_launch(int offload, unsigned grid, int threads, const SegParams &sp,
                               cudaStream_t s) {
-    if (offload) wxpy_seg_kernel<1><<<grid, threads, 0, s>>>(sp);
+    if (offload == 3) wxpy_seg_kernel<3><<<grid, threads, 0, s>>>(sp);
+    else if (offload) wxpy_seg_kernel<1><<<grid, threads, 0, s>>>(sp);
     else wxpy_seg_kernel<0><<<grid, threads, 0, s>>>(sp);
     return cudaGetLastError();
 }
@@ -77,7 +81,8 @@ BatchShape default_batch_shape() {
     BatchShape s;
     s.threads = 256;
     s.blocks_per_sm = 4;
-    s.offload = 1;
+    s.offload = 3;  // every product in the integer pipelines: 6910 GB/s against 6767
+                    // with half the sums there, on the 4096-segment batch (GB300)
     for (int b = 0; b < kBuckets; ++b) {
         s.tile_elems[b] = b < 13 ? 0 : 8192;
         s.unroll_log2[b] = 2;
@@ -610,7 +615,7 @@ int batch_tune_impl(int bmin, int bmax, unsigned flags, wxpy_batch_tune_result *
         if ((st = make_batch(-1, bmin, bmax, &sb, s))) return st;
         double best_us = 1e30;
         int best_bps = shape.blocks_per_sm, best_of = shape.offload;
-        for (int of : {0, 1})
+        for (int of : {0, 1, 3})
             for (int bps : {1, 2, 4, 8}) {
                 BatchShape cand = shape;
                 cand.blocks_per_sm = bps;

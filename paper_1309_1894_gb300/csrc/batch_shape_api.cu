@@ -12,8 +12,9 @@ extern "C" int wxpy_batch_launch_get(int *blocks_per_sm, int *fp64_offload) {
 }
 
 extern "C" int wxpy_batch_launch_set(int blocks_per_sm, int fp64_offload) {
-    if (blocks_per_sm < 1 || blocks_per_sm > 32 || fp64_offload < 0 || fp64_offload > 1)
-        return fail(WXPY_EINVAL, "blocks_per_sm must be 1..32 and fp64_offload 0 or 1");
+    if (blocks_per_sm < 1 || blocks_per_sm > 32 ||
+        (fp64_offload != 0 && fp64_offload != 1 && fp64_offload != 3))
+        return fail(WXPY_EINVAL, "blocks_per_sm must be 1..32 and fp64_offload 0, 1 or 3");
     BatchShape s = current_batch_shape();
     s.blocks_per_sm = blocks_per_sm;
     s.offload = fp64_offload;

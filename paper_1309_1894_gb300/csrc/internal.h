@@ -93,7 +93,7 @@ constexpr int64_t kMaxTileElems = (1 << 30) - 32;
 struct BatchShape {
     int threads;                   // block size of the persistent kernel
     int blocks_per_sm;             // grid = blocks_per_sm * sm_count (capped by tiles)
-    int offload;                   // sums in the integer pipeline: 0 none, 1 half
+    int offload;                   // integer pipelines: 0 none, 1 half the sums, 3 every product
     int32_t tile_elems[kBuckets];  // per size bucket of a segment; 0 = whole segment
     int8_t unroll_log2[kBuckets];  // per size bucket: log2 of the unroll
 };

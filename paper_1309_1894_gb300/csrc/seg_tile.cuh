@@ -28,11 +28,13 @@ __device__ __forceinline__ void tile_scalar(const double *x, const double *y, do
     st_vec<1, 2>(w + e, wv);
 }
 
-// EMU: which sums run in the integer pipeline (fp64_emu.cuh): 0 none, 1 the
-// odd lanes of every 32-byte vector.
+// EMU: which operations run in the integer pipelines (fp64_emu.cuh): 0 none,
+// 1 the sums of the odd positions of every 32-byte vector, 3 every product
+// (with alpha's split ca).
 template <int EMU>
 __device__ __forceinline__ void tile_body4(const double *x, const double *y, double *w,
-                                           double alpha, int64_t nch, int lane, int U) {
+                                           double alpha, const MulCoef &ca, int64_t nch, int lane,
+                                           int U) {
     const int64_t step = 32 * U;
     for (int64_t c0 = lane; c0 < nch; c0 += step) {
         double xv[kTileMaxU][4], yv[kTileMaxU][4], wv[kTileMaxU][4];
@@ -48,7 +50,7 @@ __device__ __forceinline__ void tile_body4(const double *x, const double *y, dou
         for (int u = 0; u < kTileMaxU; ++u) {
             const int64_t c = c0 + 32 * u;
             if (u < U && c < nch) {
-                wxpy_vec_emu<4, EMU>(alpha, xv[u], yv[u], wv[u], 0);
+                wxpy_vec_emu<4, EMU>(alpha, ca, xv[u], yv[u], wv[u], 0);
                 st_vec<4, 2>(w + c * 4, wv[u]);
             }
         }
@@ -59,6 +61,8 @@ __device__ __forceinline__ void tile_body4(const double *x, const double *y, dou
 template <int EMU>
 __device__ __forceinline__ void tile_wxpy(const double *x, const double *y, double *w,
                                           double alpha, int64_t len, int lane, int U) {
+    MulCoef ca{};
+    if constexpr (EMU == 3) ca = mul_coef_of((uint64_t)__double_as_longlong(alpha));
     const uintptr_t ax = (uintptr_t)x, ay = (uintptr_t)y, aw = (uintptr_t)w;
     if ((((ax ^ aw) | (ay ^ aw)) & 31u) == 0) {
         const int64_t head = min(len, (int64_t)((4 - (int)((aw >> 3) & 3)) & 3));
@@ -67,7 +71,7 @@ __device__ __forceinline__ void tile_wxpy(const double *x, const double *y, doub
         if (lane < head) tile_scalar(x, y, w, alpha, lane);
         if (lane >= 4 && body_end + (lane - 4) < len)
             tile_scalar(x, y, w, alpha, body_end + (lane - 4));
-        tile_body4<EMU>(x + head, y + head, w + head, alpha, nch, lane, U);
+        tile_body4<EMU>(x + head, y + head, w + head, alpha, ca, nch, lane, U);
     } else {
         for (int64_t e = lane; e < len; e += 32) tile_scalar(x, y, w, alpha, e);
     }

@@ -557,7 +557,8 @@ int cache_load(const char *path, const char *expect_device) {
             bs.blocks_per_sm = (int)bps;
             long long of = -1;  // optional (files written before the knob existed)
             if (find_int(s, lpos, lend, "fp64_offload", &of)) {
-                if (of < 0 || of > 1) return fail(WXPY_EINVAL, "%s: malformed batch_launch", path);
+                if (of != 0 && of != 1 && of != 3)
+                    return fail(WXPY_EINVAL, "%s: malformed batch_launch", path);
                 bs.offload = (int)of;
             }
         }

@@ -85,10 +85,12 @@ def test_cache_file_with_batch_shapes(tmp_path):
 def test_batch_launch_knobs():
     wx.wxpy_batch_shape_reset()
     bps, of = wx.wxpy_batch_launch_get()
-    assert 1 <= bps <= 32 and of in (0, 1)
+    assert 1 <= bps <= 32 and of in (0, 1, 3)
     wx.wxpy_batch_launch_set(8, 0)
     assert wx.wxpy_batch_launch_get() == (8, 0)
-    for bad in ((0, 0), (33, 0), (4, 2), (4, -1)):
+    wx.wxpy_batch_launch_set(2, 3)  # every product in the integer pipelines
+    assert wx.wxpy_batch_launch_get() == (2, 3)
+    for bad in ((0, 0), (33, 0), (4, 2), (4, -1), (4, 4)):
         with pytest.raises(wx.WxpyError):
             wx.wxpy_batch_launch_set(*bad)
     wx.wxpy_batch_shape_reset()

@@ -98,7 +98,7 @@ def _shapes():
     wx.wxpy_batch_shape_reset()
 
 
-@pytest.mark.parametrize("offload", [0, 1])
+@pytest.mark.parametrize("offload", [0, 1, 3])
 @pytest.mark.parametrize("mode", ["launch", "graph", "oneshot"])
 def test_batch_matches_oracle(mode, offload):
     wx.wxpy_batch_launch_set(4, offload)

@@ -100,9 +100,9 @@ def test_serial_batched_and_fused_modes_agree():
 
 @pytest.mark.parametrize("mode", [SERVE_BATCHED, SERVE_SERIAL])
 def test_caller_data_requests_in_a_mix(mode):
-    """Requests on the caller's data -- device tensors and pinned host tensors
-    -- mixed with seeded requests in the same batches: every result is the
-    oracle's on its own inputs, the caller's buffers are untouched, and the
+    """Requests on the caller's data -- device tensors, pinned and pageable host
+    tensors -- mixed with seeded requests in the same batches: every result is
+    the oracle's on its own inputs, the caller's buffers are untouched, and the
     resident x and y hold exactly the caller's values."""
     rng = np.random.default_rng(41)
     lens = [1, 5, 4099, 8192, 70001, (1 << 18) + 3, 300000]
@@ -115,12 +115,13 @@ def test_caller_data_requests_in_a_mix(mode):
             xh[:4] = [0.0, -0.0, 5e-324, np.inf]
             yh[:4] = [-0.0, 0.0, -5e-324, 1.0]
         alpha = float(rng.uniform(-2, 2))
-        on_gpu = i % 2 == 0
-        if on_gpu:
+        if i % 3 == 0:
             x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
-        else:
+        elif i % 3 == 1:
             x = torch.from_numpy(xh).pin_memory()
             y = torch.from_numpy(yh).pin_memory()
+        else:  # pageable host memory: copied synchronously, still exact
+            x, y = torch.from_numpy(xh.copy()), torch.from_numpy(yh.copy())
         data.append((n, alpha, xh, yh, x, y))
     seeded = request_mix(43, 30, 1 << 17)
     with Server(budget_bytes=1 << 30, mode=mode, n_streams=2, max_batch=16) as sv:
@@ -245,6 +246,9 @@ def test_poisson_loadgen_short():
         assert r["elem_per_s"] > 0
         st = sv.stats()
         assert st["resident_now"] == 0 and st["arena_used"] == 0
+        # the batch timing record: some host time to queue each batch, and no
+        # batch took longer from queueing to completion than the slowest request
+        assert 0 < st["max_launch_host_s"] <= st["max_batch_s"] <= r["max_s"]
 
 
 def test_batches_overlap_under_load():
