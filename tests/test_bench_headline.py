@@ -116,3 +116,11 @@ def test_in_place_alpha_is_contracting():
     assert bench.call_pointers(px, py, pw, 5, 1, "w=x") == (1008, 2008, 1008)
     assert bench.call_pointers(px, py, pw, 5, 1, "w=y") == (1008, 2008, 2008)
     assert bench.call_pointers(px, py, pw, 5, 1, "distinct") == (1008, 2008, 3008)
+
+
+def test_served_only_rejects_unknown_modes():
+    import subprocess
+    r = subprocess.run([sys.executable, "bench.py", "--served-only", "batched,sideways"],
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "unknown served modes" in r.stderr
