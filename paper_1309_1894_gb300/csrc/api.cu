@@ -582,7 +582,7 @@ int wxpy_reference(int64_t n, double alpha, const double *x, const double *y, do
     if (st != WXPY_OK || n == 0) return st;
     const int64_t grid = (n + 255) / 256;
     if (grid > 0x7fffffff) return fail(WXPY_EINVAL, "n too large for the reference variant");
-    SingleArgs a{x, y, w, alpha, n, 0, 0};
+    SingleArgs a{x, y, w, alpha, n, 0, 0, MulCoef{}};
     cudaError_t e = injected_launch_error();
     if (e == cudaSuccess) e = launch_reference((unsigned)grid, 256u, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "reference kernel launch");

@@ -471,7 +471,7 @@ int make_batch(int b, int bmin, int bmax, SynthBatch *sb, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(sb->wref.p, 0xff, bytes, s);
     for (size_t i = 0; i < ns.size() && e == cudaSuccess; ++i) {
         const wxpy_desc &d = sb->host[i];
-        SingleArgs a{d.x, d.y, (double *)sb->wref.p + (d.w - (double *)sb->w.p), d.alpha, d.n, 0, 0};
+        SingleArgs a{d.x, d.y, (double *)sb->wref.p + (d.w - (double *)sb->w.p), d.alpha, d.n, 0, 0, MulCoef{}};
         e = launch_reference((unsigned)((d.n + 255) / 256), 256u, a, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

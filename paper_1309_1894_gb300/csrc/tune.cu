@@ -216,7 +216,7 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
 
     // Reference results of Sec. 2: the plain variant on the same inputs.
     {
-        SingleArgs a{p.x, p.y, sc.wref, p.alpha, n, 0, 0};
+        SingleArgs a{p.x, p.y, sc.wref, p.alpha, n, 0, 0, MulCoef{}};
         e = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(sc.s);
         if (e != cudaSuccess) return fail_cuda(e, "tuner reference run");
@@ -315,7 +315,7 @@ int tune_impl(int64_t n, unsigned flags, wxpy_tune_result *out) {
         const double *x, *y;
         double *w;
         batch_operands(p, sc, flush, i, &x, &y, &w);
-        SingleArgs a{x, y, w, p.alpha, n, 0, 0};
+        SingleArgs a{x, y, w, p.alpha, n, 0, 0, MulCoef{}};
         const cudaError_t le = launch_reference((unsigned)((n + 255) / 256), 256u, a, sc.s);
         return le == cudaSuccess ? WXPY_OK : fail_cuda(le, "tuner reference timing");
     }, &ref_us);
