@@ -303,3 +303,23 @@ def test_backfill_admission(admission_us):
             sv.release(t)
         st = sv.stats()
         assert st["head_wait_frag_s"] + st["head_wait_full_s"] > 0.1
+
+
+def test_tile_list_grows_for_a_batch_of_short_tiles():
+    """A batch shape with 32-element tiles makes one batch need far more tile
+    records than a stream's list was sized for (its share of the budget at
+    8192-element tiles): the scheduler reallocates the idle slot's staging
+    region before queueing the batch, and every result is still exact."""
+    try:
+        for b in range(13, 23):
+            wx.wxpy_batch_shape_set(b, 32, 1)
+        reqs = [(int(n), float(a), 7000 + i) for i, (n, a) in enumerate(zip(
+            [(1 << 22) + 5, (1 << 21) + 3, 1 << 20, 123457, 8193, 1, 77],
+            synth.uniform_pm2(71, synth.TAG_ALPHA, 7)))]
+        # 2 GiB budget, 2 streams: a stream's list starts at 1 GiB / (24 x 8192) + 16,
+        # about 5.5k records; the first request alone is 131k tiles of 32 elements
+        out, st = run_requests(SERVE_BATCHED, reqs, n_streams=2, max_batch=16)
+        for (n, a, s) in reqs:
+            assert torch.equal(out[s].view(torch.int64), alone(n, a, s).view(torch.int64)), n
+    finally:
+        wx.wxpy_batch_shape_reset()
