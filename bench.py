@@ -52,8 +52,8 @@ SWEEP_K = range(10, 29)
 OFFSETS = (0, 8, 24)
 ALIASES = ("distinct", "w=x", "w=y")
 DOMINANT_K = 28
-WORKLOAD = ("FP64 wxpy size sweep: n = 2^k, 2^k+3, k = 10..28, offsets 0/8/24 B, "
-            "alias distinct/w=x/w=y, 38 calls per step")
+WORKLOAD = ("FP64 wxpy sweep n=2^k,2^k+3 k=10..28, offsets 0/8/24 B, "
+            "alias distinct/w=x/w=y, 38 calls/step")
 # The CPU sample both arms time: the sweep's calls with n <= 2^24 + 3.
 CPU_SAMPLE_K = 24
 CPU_SAMPLE = ("one pass = the sweep's 30 calls with k = 10..24 (n = 2^k and 2^k+3, same "
@@ -541,7 +541,7 @@ def headline(result):
     line["config"] = {k: cfg[k] for k in ("workload", "parallelism", "variant_n_2e28")
                       if k in cfg}
     if "step_bytes" in cfg:
-        line["config"]["l2"] = f"no flush: {cfg['step_bytes'] / 1e9:.1f} GB/step > L2"
+        line["config"]["l2"] = f"{cfg['step_bytes'] / 1e9:.1f} GB/step > L2, no flush"
     line["config"]["cpu_sample"] = CPU_SAMPLE_SHORT
     rf = result.get("roofline")
     if rf:
