@@ -340,9 +340,8 @@ int wxpy_vecops_status(void);
  * wxpy_reduce_workspace_bytes(n) bytes, 16-byte aligned, disjoint from the
  * vectors and result, owned by the caller; the call overwrites it, so calls in
  * flight at the same time need separate workspaces.  Nothing is allocated.
- * When x, y, w (and z) are all 32-byte aligned, the inputs stream through
- * shared memory by bulk asynchronous copies (a producer warp and eight
- * consumer warps per block, every wait bounded; see wxpy_reduce_status);
+ * When x, y, w (and z) are all 32-byte aligned, the kernel of the current
+ * configuration (wxpy_reduce_variant) reads them as 32-byte vectors;
  * otherwise every element is read and written on its own (same bits).
  * Errors: WXPY_EINVAL (bad argument, workspace too small), WXPY_EOVERLAP,
  * WXPY_ECUDA. */
@@ -361,19 +360,22 @@ int wxpy_dot(int64_t n, double alpha, const double *x, const double *y, double *
  * and wxpy_reduce_sum_levels. */
 int wxpy_reduce_pipes(int mul_sixteenths);
 
-/* wxpy_norm2 on the register-loaded kernel: how many of the three tree
- * levels summed inside a thread (the first three of each tile) run as the
+/* wxpy_norm2: how many of the leading tree levels of each tile run as the
  * exactly rounded integer-pipeline sum of two non-negative values instead of
- * FP64 instructions: 0..3, -1 the default.  Same bits either way.
- * Process-wide. */
+ * FP64 instructions: 0..6, -1 the default.  The register-loaded kernel sums
+ * its first three levels inside a thread and applies at most 3; the
+ * warp-tiled kernels sum six there and apply all; the staged kernels none.
+ * Same bits either way.  Process-wide. */
 int wxpy_reduce_sum_levels(int levels);
 
 /* The kernel of wxpy_norm2 / wxpy_dot for 32-byte co-aligned pointers
  * (other alignments always take the element path): 0 register-loaded (a
  * block of 256 threads per tile, 32-byte loads into registers); 1, 2, 3
  * staged through a shared-memory ring of bulk copies with (ring stages,
- * resident blocks per SM) = (4, 2), (3, 3), (2, 3); -1 the default.  Same
- * bits for every variant.  Process-wide. */
+ * resident blocks per SM) = (4, 2), (3, 3), (2, 3); 4, 5, 6 warp-tiled (one
+ * warp per tile, no block barrier; rows loaded together, resident 128-thread
+ * blocks per SM) = (2, 5), (4, 4), (4, 3); -1 the default.  Same bits for
+ * every variant.  Process-wide. */
 int wxpy_reduce_variant(int variant);
 
 typedef struct wxpy_reduce_tune_result {
@@ -393,8 +395,9 @@ typedef struct wxpy_reduce_tune_result {
  * register-loaded kernel with every operation in FP64 gives the reference w
  * and result; every candidate configuration (the register-loaded kernel at
  * product shares 0, 4, .., 16 sixteenths; for norm2, 1..3 integer tree
- * levels at the best share and at half of it; the three staged shapes at the
- * best share) is run once and compared with it bit for bit -- a single
+ * levels at the best share and at half of it; the three staged shapes and
+ * the three warp-tiled shapes at the best share; for norm2, 2, 4 and 6
+ * integer tree levels in the fastest warp-tiled shape) is run once and compared with it bit for bit -- a single
  * differing bit of w or of the result rejects it -- and timed as the median
  * of five runs of three back-to-back calls, each run after an L2 flush.  The fastest verified configuration
  * becomes the operation's configuration for later calls whose knobs are left

@@ -12,7 +12,9 @@
 // configuration whose w or result differs by a single bit is rejected.
 // Candidates, per operation: the register-loaded form at product shares 0, 4,
 // .., 16 sixteenths; for norm2, one to three integer tree levels at the best
-// share and at half of it; the three staged shapes at the best share.  Timing:
+// share and at half of it; the three staged shapes and the three warp-tiled
+// shapes at the best share; for norm2, 2, 4 and 6 integer tree levels in the
+// fastest warp-tiled shape.  Timing:
 // median of five runs of three back-to-back calls, each run after an L2 flush
 // and a short device delay (w never aliases an input here, so no restore is
 // needed).
@@ -122,8 +124,10 @@ int tune_kind(int kind, int64_t n, RScratch &sc, wxpy_reduce_tune_result *res) {
     ReduceConfig best{0, 0, 0};
     double best_us = 0.0;
     bool have = false;
+    double last_us = 0.0;  // the last candidate's time, 0 when it was rejected
     auto consider = [&](ReduceConfig c) -> int {
         ++candidates;
+        last_us = 0.0;
         unsigned long long mism = 0;
         int s2 = run_checked(kind, n, c, sc, &mism);
         if (s2 != WXPY_OK) return s2;
@@ -133,6 +137,7 @@ int tune_kind(int kind, int64_t n, RScratch &sc, wxpy_reduce_tune_result *res) {
         }
         double us = 0.0;
         if ((s2 = time_config(kind, n, c, sc, &us)) != WXPY_OK) return s2;
+        last_us = us;
         if (!have || us < best_us) {
             best = c;
             best_us = us;
@@ -153,6 +158,20 @@ int tune_kind(int kind, int64_t n, RScratch &sc, wxpy_reduce_tune_result *res) {
     }
     for (int v = 1; v <= 3; ++v)
         if ((st = consider(ReduceConfig{v, bmul, 0})) != WXPY_OK) return st;
+    // the warp-tiled shapes at the best share; for norm2 then 2, 4 and 6
+    // integer tree levels in the shape that did best among them
+    double wbest_us = 0.0;
+    int wbest = 4;
+    for (int v = 4; v <= 6; ++v) {
+        if ((st = consider(ReduceConfig{v, bmul, 0})) != WXPY_OK) return st;
+        if (last_us > 0.0 && (wbest_us == 0.0 || last_us < wbest_us)) {
+            wbest_us = last_us;
+            wbest = v;
+        }
+    }
+    if (kind == 0)
+        for (int l = 2; l <= 6; l += 2)
+            if ((st = consider(ReduceConfig{wbest, bmul, l})) != WXPY_OK) return st;
     double def_us = 0.0;
     if ((st = time_config(kind, n, reduce_default(kind), sc, &def_us)) != WXPY_OK) return st;
     reduce_tuned_store(kind, &best);

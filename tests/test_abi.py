@@ -181,10 +181,10 @@ def test_vecops_validation_before_cuda(lib):
     assert lib.wxpy_debug_vecops_drop_tile(-1) == 0
     assert lib.wxpy_debug_reduce_drop_chunk(-2) == wx.WXPY_EINVAL
     assert lib.wxpy_debug_reduce_drop_chunk(-1) == 0
-    for bad in (-2, 4):
+    for bad in (-2, 7):
         assert lib.wxpy_reduce_variant(bad) == wx.WXPY_EINVAL
     assert lib.wxpy_reduce_variant(-1) == 0
-    for bad in (-2, 4):
+    for bad in (-2, 7):
         assert lib.wxpy_reduce_sum_levels(bad) == wx.WXPY_EINVAL
     assert lib.wxpy_reduce_sum_levels(-1) == 0
 

@@ -59,7 +59,7 @@ def want(kind, alpha, xh, yh, zh):
 
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
-@pytest.mark.parametrize("variant", [-1, 1, 3])
+@pytest.mark.parametrize("variant", [-1, 1, 3, 4, 6])
 @pytest.mark.parametrize("mul", [-1, 0, 5, 16])
 @pytest.mark.parametrize("offs", [(0, 0, 0, 0), (8, 8, 8, 8), (0, 16, 8, 24)])
 def test_parity(kind, variant, mul, offs):
@@ -75,7 +75,7 @@ def test_parity(kind, variant, mul, offs):
 
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
-@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("mul", [-1, 0, 7])
 @pytest.mark.parametrize("offs", [(0, 0, 0, 0), (32, 64, 96, 160), (16, 16, 16, 16)])
 def test_many_tiles_per_block(kind, variant, mul, offs):
@@ -108,6 +108,37 @@ def test_integer_tree_sums(suml, mul):
         assert same_scalar(r_got, r_want), (n, r_got, r_want)
 
 
+@pytest.mark.parametrize("variant", [4, 5, 6])
+@pytest.mark.parametrize("suml", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("mul", [0, 9, 16])
+def test_warp_tiled_integer_tree_sums(variant, suml, mul):
+    """norm2 on the warp-tiled kernels with the first 1..6 tree levels (all
+    six of a thread's) summed in the integer pipelines: every size of the
+    parity set and several tiles per warp with a ragged last tile."""
+    wx.wxpy_reduce_variant(variant)
+    wx.wxpy_reduce_sum_levels(suml)
+    wx.wxpy_reduce_pipes(mul)
+    for n in SIZES + ((1 << 23) + 4 * T + 5,):
+        alpha, xh, yh = synth.vectors(synth.BASE_SEED + 545 + n, n)
+        w_got, r_got = run("norm2", alpha, xh, yh, None, (0, 0, 0, 0))
+        w_want, r_want = oracle.wxpy_norm2(alpha, xh, yh)
+        assert same_vec(w_got, w_want), n
+        assert same_scalar(r_got, r_want), (n, r_got, r_want)
+
+
+def test_register_loaded_applies_three_levels():
+    """The register-loaded kernel sums three levels inside a thread: asked for
+    more it applies three and stays exact."""
+    wx.wxpy_reduce_variant(0)
+    wx.wxpy_reduce_sum_levels(6)
+    wx.wxpy_reduce_pipes(16)
+    n = 5 * T + 3
+    alpha, xh, yh = synth.vectors(synth.BASE_SEED + 546, n)
+    w_got, r_got = run("norm2", alpha, xh, yh, None, (0, 0, 0, 0))
+    w_want, r_want = oracle.wxpy_norm2(alpha, xh, yh)
+    assert same_vec(w_got, w_want) and same_scalar(r_got, r_want)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """The producer owning chunk 11 stops before copying it: that block's
     consumers give up after their one-second bound, the host reads
@@ -134,9 +165,11 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("kind", ["norm2", "dot"])
 @pytest.mark.parametrize("mul", [0, 16])
-@pytest.mark.parametrize("suml", [0, 3])
+@pytest.mark.parametrize("suml", [0, 3, 6])
 @pytest.mark.parametrize("offs", [(0, 0, 0, 0), (8, 8, 8, 8)])
-def test_special_and_wide_values(kind, mul, suml, offs):
+@pytest.mark.parametrize("variant", [-1, 5])
+def test_special_and_wide_values(kind, mul, suml, offs, variant):
+    wx.wxpy_reduce_variant(variant)
     wx.wxpy_reduce_pipes(mul)
     wx.wxpy_reduce_sum_levels(suml)
     sv = np.array(pins.special_values())
@@ -278,11 +311,12 @@ def test_configuration_search(tmp_path):
         for r in res:
             assert r["rejected"] == 0, r
             # norm2: 5 product shares, 3 tree levels at the best share and at half of it
-            # (one fewer set when half equals the best), 3 staged shapes; dot: 5 + 3
+            # (one fewer set when half equals the best), 3 staged shapes, 3 warp-tiled
+            # shapes, 3 tree-level counts in the best of those; dot: 5 + 3 + 3
             if r["kind"] == 0:
-                assert r["candidates"] in (5 + 3 + 3, 5 + 6 + 3), r
+                assert r["candidates"] in (5 + 3 + 3 + 3 + 3, 5 + 6 + 3 + 3 + 3), r
             else:
-                assert r["candidates"] == 8 and r["sum_levels"] == 0, r
+                assert r["candidates"] == 11 and r["sum_levels"] == 0, r
             assert 0 < r["best_us"] <= r["default_us"] * 1.5, r
             assert wx.wxpy_reduce_tuned_get(r["kind"]) == (r["variant"], r["mul_sixteenths"],
                                                            r["sum_levels"])
@@ -334,11 +368,13 @@ def test_squares_one_per_tile():
     y = torch.zeros_like(x)
     with np.errstate(over="ignore", invalid="ignore"):
         want = vals * vals
-    for mul in (0, 16):
+    for variant, mul, suml in ((0, 0, 0), (0, 16, 3), (4, 16, 6), (6, 0, 6)):
+        wx.wxpy_reduce_variant(variant)
         wx.wxpy_reduce_pipes(mul)
+        wx.wxpy_reduce_sum_levels(suml)
         ws = wx.reduce_workspace(n)
         wx.wxpy_norm2(1.0, x, y, workspace=ws)
         torch.cuda.synchronize()
         sums = ws[256 + 8 * first: 256 + 8 * (first + len(vals))].cpu().numpy().view(np.float64)
         ok = (sums.view(np.uint64) == want.view(np.uint64)) | (np.isnan(sums) & np.isnan(want))
-        assert ok.all(), (mul, vals[~ok][:5], sums[~ok][:5], want[~ok][:5])
+        assert ok.all(), (variant, mul, suml, vals[~ok][:5], sums[~ok][:5], want[~ok][:5])

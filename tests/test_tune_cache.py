@@ -131,7 +131,10 @@ def test_reduce_config_set_get_clear():
     wx.wxpy_reduce_tuned_set(1, 0, 16, 0)
     wx.wxpy_tune_clear()  # drops the searched configurations too
     assert wx.wxpy_reduce_tuned_get(1) == (-1, -1, -1)
-    for bad in ((2, 0, 16, 0), (-1, 0, 16, 0), (0, 4, 16, 0), (0, 0, 17, 0), (0, 0, 16, 4),
+    wx.wxpy_reduce_tuned_set(0, 5, 16, 6)  # warp-tiled: six levels inside a thread
+    assert wx.wxpy_reduce_tuned_get(0) == (5, 16, 6)
+    wx.wxpy_reduce_tuned_set(0, -1, -1, -1)
+    for bad in ((2, 0, 16, 0), (-1, 0, 16, 0), (0, 7, 16, 0), (0, 0, 17, 0), (0, 0, 16, 7),
                 (1, 0, 16, 1)):  # dot's terms can be negative: no integer tree sums
         with pytest.raises(wx.WxpyError) as e:
             wx.wxpy_reduce_tuned_set(*bad)
@@ -156,7 +159,8 @@ def test_load_reduce_section(tmp_path):
 
 @pytest.mark.parametrize("entry", [{"kind": 2, "variant": 0, "mul_sixteenths": 2, "sum_levels": 0},
                                    {"kind": 1, "variant": 0, "mul_sixteenths": 2, "sum_levels": 1},
-                                   {"kind": 0, "variant": 4, "mul_sixteenths": 2, "sum_levels": 0},
+                                   {"kind": 0, "variant": 7, "mul_sixteenths": 2, "sum_levels": 0},
+                                   {"kind": 0, "variant": 4, "mul_sixteenths": 2, "sum_levels": 7},
                                    {"kind": 0, "variant": 0, "mul_sixteenths": 2}])
 def test_malformed_reduce_entry_stores_nothing(tmp_path, entry):
     path = tmp_path / "bad.json"
