@@ -1289,7 +1289,8 @@ def main():
                     help="profiling mode: only run wxpy() on n = SINGLE, --reps times")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--variant", type=int, default=-1,
-                    help="profiling mode: force this variant id instead of the tuned one")
+                    help="profiling mode: force this variant id instead of the tuned one "
+                         "(with --vecop norm2 or dot: the reduction kernel variant)")
     ap.add_argument("--vecop", default="",
                     help="profiling mode: only run this kernel (batch: SINGLE segments; axpbypcz, axpby, maxpy4, maxpy8, "
                          "pointwise_mult, norm2, dot; serve: one 64-request server batch with "
@@ -1405,6 +1406,7 @@ def run_vecop(args):
         ws = wx.reduce_workspace(n)
         res = torch.empty(1, dtype=torch.float64, device="cuda")
         wx.wxpy_reduce_pipes(mul)
+        wx.wxpy_reduce_variant(args.variant)  # -1: the default kernel
     for _ in range(args.reps):
         if args.vecop == "norm2":
             wx.wxpy_norm2(0.5, v[0], v[1], w=v[2], result=res, workspace=ws)
