@@ -5,11 +5,30 @@
 
 #include <cstdint>
 
+// The cores (mul_coef_of, mul_rn_core, sqr_rn_core) also compile as plain
+// host C++, so the host can check them against its own IEEE multiply.
+#ifdef __CUDACC__
+#define WX_MUL_FN __host__ __device__ __forceinline__
+#else
+#define WX_MUL_FN inline
+#endif
+
 namespace wx {
 
+#ifdef __CUDACC__
 static __device__ __noinline__ uint64_t mul_rn_hw_bits(uint64_t ua, uint64_t ub) {
     return (uint64_t)__double_as_longlong(
         __dmul_rn(__longlong_as_double((long long)ua), __longlong_as_double((long long)ub)));
+}
+#endif
+
+// Bits sh .. sh + 31 of the 64-bit word hi:lo, 0 <= sh < 32.
+WX_MUL_FN uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t sh) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_r(lo, hi, sh);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> sh);
+#endif
 }
 
 // RN(a * b) in the integer pipelines (multiply-adds on the FMA pipeline,
@@ -38,7 +57,7 @@ struct MulCoef {
     uint32_t k;   // sign << 31 plus (biased exponent - 1024) << 20, modulo 2^32
 };
 
-__host__ __device__ inline MulCoef mul_coef_of(uint64_t ua) {
+WX_MUL_FN MulCoef mul_coef_of(uint64_t ua) {
     const uint32_t ah = (uint32_t)(ua >> 32);
     const uint32_t ea = (ah >> 20) & 0x7FFu;
     MulCoef c;
@@ -51,7 +70,7 @@ __host__ __device__ inline MulCoef mul_coef_of(uint64_t ua) {
 
 // The fast path of RN(c * b): the result's bits, and `slow` set when the
 // operands or the result leave it (the bits are then meaningless).
-__device__ __forceinline__ uint64_t mul_rn_core(const MulCoef &c, uint64_t ub, bool &slow) {
+WX_MUL_FN uint64_t mul_rn_core(const MulCoef &c, uint64_t ub, bool &slow) {
     const uint32_t bh = (uint32_t)(ub >> 32), bl = (uint32_t)ub;
     const uint32_t eb = (bh >> 20) & 0x7FFu;
     const uint32_t b1 = (bh & 0xFFFFFu) | 0x100000u;
@@ -63,8 +82,8 @@ __device__ __forceinline__ uint64_t mul_rn_core(const MulCoef &c, uint64_t ub, b
     const uint32_t tl = (uint32_t)top, th = (uint32_t)(top >> 32);
     const uint32_t t = th >> 9;                     // bit 105 of P
     const uint32_t sh = 20 + t;                     // significand = (top:w1) >> sh
-    const uint32_t m0l = __funnelshift_r(w1, tl, sh);
-    const uint32_t m0h = __funnelshift_r(tl, th, sh);  // < 2^21, hidden bit at bit 20
+    const uint32_t m0l = funnel_r(w1, tl, sh);
+    const uint32_t m0h = funnel_r(tl, th, sh);  // < 2^21, hidden bit at bit 20
     const uint32_t rnd = (w1 >> (sh - 1)) & 1u;
     const uint32_t stk = (w0 | (w1 << (33 - sh))) != 0u;
     const uint32_t inc = rnd & (stk | m0l);
@@ -80,7 +99,7 @@ __device__ __forceinline__ uint64_t mul_rn_core(const MulCoef &c, uint64_t ub, b
 // 2 A1 A0 2^32 + A0^2 for the limbs A1 (21 bits, hidden bit included) and A0
 // (32 bits).  The sign is always clear; the biased exponent is
 // 2 ea - 1023 + t.  `slow` as in mul_rn_core.
-__device__ __forceinline__ uint64_t sqr_rn_core(uint64_t ua, bool &slow) {
+WX_MUL_FN uint64_t sqr_rn_core(uint64_t ua, bool &slow) {
     const uint32_t ah = (uint32_t)(ua >> 32), a0 = (uint32_t)ua;
     const uint32_t ea = (ah >> 20) & 0x7FFu;
     const uint32_t a1 = (ah & 0xFFFFFu) | 0x100000u;
@@ -92,8 +111,8 @@ __device__ __forceinline__ uint64_t sqr_rn_core(uint64_t ua, bool &slow) {
     const uint32_t tl = (uint32_t)top, th = (uint32_t)(top >> 32);
     const uint32_t t = th >> 9;
     const uint32_t sh = 20 + t;
-    const uint32_t m0l = __funnelshift_r(w1, tl, sh);
-    const uint32_t m0h = __funnelshift_r(tl, th, sh);
+    const uint32_t m0l = funnel_r(w1, tl, sh);
+    const uint32_t m0h = funnel_r(tl, th, sh);
     const uint32_t rnd = (w1 >> (sh - 1)) & 1u;
     const uint32_t stk = (w0 | (w1 << (33 - sh))) != 0u;
     const uint32_t inc = rnd & (stk | m0l);
@@ -103,6 +122,7 @@ __device__ __forceinline__ uint64_t sqr_rn_core(uint64_t ua, bool &slow) {
     return (((uint64_t)hw << 32) | m0l) + inc;
 }
 
+#ifdef __CUDACC__
 __device__ __forceinline__ uint64_t sqr_rn_bits(uint64_t ua) {
     bool slow = false;
     uint64_t bits = sqr_rn_core(ua, slow);
@@ -126,4 +146,8 @@ __device__ __forceinline__ double mul_rn_int(double a, double b) {
                                                        (uint64_t)__double_as_longlong(b)));
 }
 
+#endif  // __CUDACC__
+
 }  // namespace wx
+
+#undef WX_MUL_FN
