@@ -34,7 +34,72 @@
 
 #include "fp64_mul.cuh"
 
+// The core (add_rn_core) also compiles as plain host C++, so the host can
+// check it against its own IEEE addition.
+#ifdef __CUDACC__
+#define WX_EMU_FN __host__ __device__ __forceinline__
+#else
+#define WX_EMU_FN inline
+#endif
+
 namespace wx {
+
+// Leading zeros of a 64-bit word, 64 for zero.
+WX_EMU_FN int clz64(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// RN(a + b) on the bit patterns ua, ub of two binary64 values, on the fast
+// path: the result's bits, and `slow` set when the operands or the result
+// leave it (the bits are then meaningless).
+WX_EMU_FN uint64_t add_rn_core(uint64_t ua, uint64_t ub, bool &slow) {
+    constexpr uint64_t kSign = 1ull << 63;
+    constexpr uint64_t kAbs = kSign - 1;
+    constexpr uint64_t kFrac = (1ull << 52) - 1;
+    constexpr uint64_t kHidden = 1ull << 52;
+    const bool a_big = (ua & kAbs) >= (ub & kAbs);
+    const uint64_t hi = a_big ? ua : ub;
+    const uint64_t lo = a_big ? ub : ua;
+    const int ehi = (int)((hi >> 52) & 0x7FF);
+    const int elo = (int)((lo >> 52) & 0x7FF);
+    // Inf/NaN, zero or subnormal operands go to the hardware.
+    slow = slow || ehi == 0x7FF || elo == 0;
+    // Branch-free: the lanes of a warp follow one path whatever the signs and
+    // exponent gaps of their operands.  Every value stays an integer bit
+    // pattern until the one reinterpretation by the caller: merging several
+    // double-valued return paths made the compiler issue FP64-pipeline
+    // instructions.
+    const int dd = ehi - elo < 63 ? ehi - elo : 63;  // 63 or more leaves only the sticky bit
+    const uint64_t H = ((hi & kFrac) | kHidden) << 10;
+    const uint64_t L0 = ((lo & kFrac) | kHidden) << 10;
+    const uint64_t L = (L0 >> dd) | (uint64_t)((L0 & ((1ull << dd) - 1)) != 0);
+    // H + L, or H - L (two's complement) when the signs differ
+    const uint64_t neg = ((hi ^ lo) & kSign) ? ~0ull : 0ull;
+    uint64_t S = H + (L ^ neg) - neg;
+    const bool zero = S == 0;  // exact cancellation rounds to +0
+    // Leading one back to bit 62: one right shift after a carry (lz == 0, with
+    // the jam bit kept), or lz - 1 left shifts after a cancellation.
+    const int lz = clz64(S);
+    const uint64_t right = (S >> 1) | (S & 1);
+    const uint64_t left = S << ((lz - 1) & 63);
+    S = lz == 0 ? right : left;
+    int e = ehi + 1 - lz;
+    // Round to nearest, ties to even, at bit 10.
+    uint64_t m = S >> 10;
+    const uint64_t rem = S & 0x3FF;
+    m += (uint64_t)(rem > 0x200 || (rem == 0x200 && (m & 1)));
+    const int carry = (int)(m >> 53);  // rounding reached the next binade
+    m >>= carry;
+    e += carry;
+    slow = slow || (!zero && (e <= 0 || e >= 0x7FF));  // subnormal or overflowing result
+    return zero ? 0ull : ((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac));
+}
+
+#ifdef __CUDACC__
 
 // The hardware sum for the rare operands the integer path leaves out, on bit
 // patterns.  Kept out of line: an inlined fallback is if-converted by the
@@ -57,48 +122,11 @@ __device__ __forceinline__ uint64_t opaque_bits(double v) {
     return b;
 }
 
-// RN(a + b) on the bit patterns ua, ub of two binary64 values.
+// RN(a + b) on the bit patterns ua, ub of two binary64 values; the hardware
+// instruction, out of line, for what the fast path leaves out.
 __device__ __forceinline__ uint64_t add_rn_bits(uint64_t ua, uint64_t ub) {
-    constexpr uint64_t kSign = 1ull << 63;
-    constexpr uint64_t kAbs = kSign - 1;
-    constexpr uint64_t kFrac = (1ull << 52) - 1;
-    constexpr uint64_t kHidden = 1ull << 52;
-    const bool a_big = (ua & kAbs) >= (ub & kAbs);
-    const uint64_t hi = a_big ? ua : ub;
-    const uint64_t lo = a_big ? ub : ua;
-    const int ehi = (int)((hi >> 52) & 0x7FF);
-    const int elo = (int)((lo >> 52) & 0x7FF);
-    // Inf/NaN, zero or subnormal operands go to the hardware at the end.
-    bool slow = ehi == 0x7FF || elo == 0;
-    // Branch-free from here to the single fallback test: the lanes of a warp
-    // follow one path whatever the signs and exponent gaps of their operands.
-    // Every value stays an integer bit pattern until the one reinterpretation
-    // at the end: merging several double-valued return paths made the
-    // compiler issue FP64-pipeline instructions.
-    const int dd = min(ehi - elo, 63);  // a gap of 63 or more leaves only the sticky bit
-    const uint64_t H = ((hi & kFrac) | kHidden) << 10;
-    const uint64_t L0 = ((lo & kFrac) | kHidden) << 10;
-    const uint64_t L = (L0 >> dd) | (uint64_t)((L0 & ((1ull << dd) - 1)) != 0);
-    // H + L, or H - L (two's complement) when the signs differ
-    const uint64_t neg = ((hi ^ lo) & kSign) ? ~0ull : 0ull;
-    uint64_t S = H + (L ^ neg) - neg;
-    const bool zero = S == 0;  // exact cancellation rounds to +0
-    // Leading one back to bit 62: one right shift after a carry (lz == 0, with
-    // the jam bit kept), or lz - 1 left shifts after a cancellation.
-    const int lz = __clzll((long long)S);
-    const uint64_t right = (S >> 1) | (S & 1);
-    const uint64_t left = S << ((lz - 1) & 63);
-    S = lz == 0 ? right : left;
-    int e = ehi + 1 - lz;
-    // Round to nearest, ties to even, at bit 10.
-    uint64_t m = S >> 10;
-    const uint64_t rem = S & 0x3FF;
-    m += (uint64_t)(rem > 0x200 || (rem == 0x200 && (m & 1)));
-    const int carry = (int)(m >> 53);  // rounding reached the next binade
-    m >>= carry;
-    e += carry;
-    slow = slow || (!zero && (e <= 0 || e >= 0x7FF));  // subnormal or overflowing result
-    uint64_t bits = zero ? 0ull : ((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac));
+    bool slow = false;
+    uint64_t bits = add_rn_core(ua, ub, slow);
     if (slow) bits = add_rn_hw_bits(ua, ub);
     return bits;
 }
@@ -142,4 +170,8 @@ __device__ __forceinline__ void wxpy_vec_emu(double alpha, const MulCoef &ca, co
     }
 }
 
+#endif  // __CUDACC__
+
 }  // namespace wx
+
+#undef WX_EMU_FN
