@@ -109,7 +109,7 @@ def kernel_source_hash() -> str:
     """Hash of the single-call kernel sources; a profile summary records it, so
     that a stale ncu traffic figure is never reported against a changed kernel."""
     h = hashlib.sha256()
-    for name in ("single_kernel.cuh", "fp64_emu.cuh"):
+    for name in ("single_kernel.cuh", "fp64_emu.cuh", "fp64_mul.cuh"):
         with open(os.path.join(ROOT, "paper_1309_1894_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -34,29 +34,22 @@
 
 #include "fp64_mul.cuh"
 
-// The core (add_rn_core) also compiles as plain host C++, so the host can
+// The sum (add_rn_with) also compiles as plain host C++, so the host can
 // check it against its own IEEE addition.
 #ifdef __CUDACC__
-#define WX_EMU_FN __host__ __device__ __forceinline__
+#define WX_EMU_FN __device__ __forceinline__
 #else
 #define WX_EMU_FN inline
 #endif
 
 namespace wx {
 
-// Leading zeros of a 64-bit word, 64 for zero.
-WX_EMU_FN int clz64(uint64_t v) {
-#ifdef __CUDA_ARCH__
-    return __clzll((long long)v);
-#else
-    return v ? __builtin_clzll(v) : 64;
-#endif
-}
-
-// RN(a + b) on the bit patterns ua, ub of two binary64 values, on the fast
-// path: the result's bits, and `slow` set when the operands or the result
-// leave it (the bits are then meaningless).
-WX_EMU_FN uint64_t add_rn_core(uint64_t ua, uint64_t ub, bool &slow) {
+// RN(a + b) on the bit patterns ua, ub of two binary64 values.  Operands and
+// results the integer path leaves out go to hw(ua, ub): the hardware
+// instruction, out of line, in the kernels (add_rn_bits below); the host's
+// check of this function passes a recorder instead.
+template <class Hw>
+WX_EMU_FN uint64_t add_rn_with(uint64_t ua, uint64_t ub, Hw hw) {
     constexpr uint64_t kSign = 1ull << 63;
     constexpr uint64_t kAbs = kSign - 1;
     constexpr uint64_t kFrac = (1ull << 52) - 1;
@@ -66,14 +59,18 @@ WX_EMU_FN uint64_t add_rn_core(uint64_t ua, uint64_t ub, bool &slow) {
     const uint64_t lo = a_big ? ub : ua;
     const int ehi = (int)((hi >> 52) & 0x7FF);
     const int elo = (int)((lo >> 52) & 0x7FF);
-    // Inf/NaN, zero or subnormal operands go to the hardware.
-    slow = slow || ehi == 0x7FF || elo == 0;
-    // Branch-free: the lanes of a warp follow one path whatever the signs and
-    // exponent gaps of their operands.  Every value stays an integer bit
-    // pattern until the one reinterpretation by the caller: merging several
-    // double-valued return paths made the compiler issue FP64-pipeline
-    // instructions.
-    const int dd = ehi - elo < 63 ? ehi - elo : 63;  // 63 or more leaves only the sticky bit
+    // Inf/NaN, zero or subnormal operands go to the hardware at the end.
+    bool slow = ehi == 0x7FF || elo == 0;
+    // Branch-free from here to the single fallback test: the lanes of a warp
+    // follow one path whatever the signs and exponent gaps of their operands.
+    // Every value stays an integer bit pattern until the one reinterpretation
+    // at the end: merging several double-valued return paths made the
+    // compiler issue FP64-pipeline instructions.
+#ifdef __CUDA_ARCH__
+    const int dd = min(ehi - elo, 63);  // a gap of 63 or more leaves only the sticky bit
+#else
+    const int dd = ehi - elo < 63 ? ehi - elo : 63;
+#endif
     const uint64_t H = ((hi & kFrac) | kHidden) << 10;
     const uint64_t L0 = ((lo & kFrac) | kHidden) << 10;
     const uint64_t L = (L0 >> dd) | (uint64_t)((L0 & ((1ull << dd) - 1)) != 0);
@@ -83,7 +80,11 @@ WX_EMU_FN uint64_t add_rn_core(uint64_t ua, uint64_t ub, bool &slow) {
     const bool zero = S == 0;  // exact cancellation rounds to +0
     // Leading one back to bit 62: one right shift after a carry (lz == 0, with
     // the jam bit kept), or lz - 1 left shifts after a cancellation.
-    const int lz = clz64(S);
+#ifdef __CUDA_ARCH__
+    const int lz = __clzll((long long)S);
+#else
+    const int lz = S ? __builtin_clzll(S) : 64;
+#endif
     const uint64_t right = (S >> 1) | (S & 1);
     const uint64_t left = S << ((lz - 1) & 63);
     S = lz == 0 ? right : left;
@@ -96,7 +97,9 @@ WX_EMU_FN uint64_t add_rn_core(uint64_t ua, uint64_t ub, bool &slow) {
     m >>= carry;
     e += carry;
     slow = slow || (!zero && (e <= 0 || e >= 0x7FF));  // subnormal or overflowing result
-    return zero ? 0ull : ((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac));
+    uint64_t bits = zero ? 0ull : ((hi & kSign) | ((uint64_t)e << 52) | (m & kFrac));
+    if (slow) bits = hw(ua, ub);
+    return bits;
 }
 
 #ifdef __CUDACC__
@@ -122,13 +125,15 @@ __device__ __forceinline__ uint64_t opaque_bits(double v) {
     return b;
 }
 
-// RN(a + b) on the bit patterns ua, ub of two binary64 values; the hardware
-// instruction, out of line, for what the fast path leaves out.
+struct AddRnHw {
+    __device__ __forceinline__ uint64_t operator()(uint64_t ua, uint64_t ub) const {
+        return add_rn_hw_bits(ua, ub);
+    }
+};
+
+// RN(a + b) on the bit patterns ua, ub of two binary64 values.
 __device__ __forceinline__ uint64_t add_rn_bits(uint64_t ua, uint64_t ub) {
-    bool slow = false;
-    uint64_t bits = add_rn_core(ua, ub, slow);
-    if (slow) bits = add_rn_hw_bits(ua, ub);
-    return bits;
+    return add_rn_with(ua, ub, AddRnHw{});
 }
 
 __device__ __forceinline__ double add_rn_int(double a, double b) {
