@@ -203,16 +203,35 @@ constexpr int max_threads() {
 // attribute), and then lets the next launch of the stream be scheduled: once
 // every block of this grid has passed this point, the next kernel's blocks
 // can take the SMs this grid frees, so its launch overlaps this grid's tail.
-// No memory is touched before the wait, so any dependence between calls (w of
-// one call is x of the next) is kept.
+// Nothing is read or written before the wait, so any dependence between calls
+// (w of one call is x of the next) is kept; only L2 prefetches are issued
+// ahead of it (prefetch_first_pass).
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Before the wait: the L2 lines of this thread's first pass of x and y are
+// requested, so that a call launched behind another one starts its DRAM
+// reads during the other's tail.  A prefetch changes no value, and the L2 is
+// where device memory is coherent, so a line the previous call is still
+// writing is read with its final contents after the wait.
+template <int VW, int U, bool XY>
+__device__ __forceinline__ void prefetch_first_pass(const SingleArgs &a, int64_t c0, int64_t tpb) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t c = c0 + u * tpb;
+        if (c < a.nchunks) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.x + a.head + c * VW));
+            if constexpr (!XY) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.y + a.head + c * VW));
+        }
+    }
+}
+
 template <int VW, int U, int GS, int CACHE, bool XY, int EMU>
 __global__ void __launch_bounds__(max_threads<VW, U, GS, XY, EMU>())
     wxpy_single_kernel(const SingleArgs a) {
+    prefetch_first_pass<VW, U, XY>(a, (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x, blockDim.x);
     pdl_enter();
     const int64_t tpb = blockDim.x;
     if constexpr (GS == 0) {
