@@ -78,22 +78,27 @@ __device__ double tile_sum(const ReduceArgs &a, int64_t tile, double (*red)[4]) 
     const int t = threadIdx.x, lane = t & 31;
     const int64_t t0 = tile * kTile + 4 * t;
     // bits 12..10: r[j] = tree over k = j, j+4 (bit 12), then j, j+2 (bit 11), then bit 10
-    double r[4][4];
+    // j in the order 0, 2, 1, 3: each pair (0, 2), (1, 3) is summed (bit 11)
+    // as soon as both are formed, so at most two level-1 vectors are live
+    double p[2][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        double lo[4], hi[4];
-        vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * j, lo);
-        vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * (j + 4), hi);
+    for (int h = 0; h < 2; ++h) {
+        double r[2][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r[j][q] = tree_add<(SUML >= 1)>(lo[q], hi[q]);
+        for (int m = 0; m < 2; ++m) {
+            const int j = h + 2 * m;
+            double lo[4], hi[4];
+            vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * j, lo);
+            vector_terms<KIND, EMU, VEC>(a, t0 + 1024 * (j + 4), hi);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[m][q] = tree_add<(SUML >= 1)>(lo[q], hi[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) p[h][q] = tree_add<(SUML >= 2)>(r[0][q], r[1][q]);
     }
     double v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        r[0][q] = tree_add<(SUML >= 2)>(r[0][q], r[2][q]);
-        r[1][q] = tree_add<(SUML >= 2)>(r[1][q], r[3][q]);
-        v[q] = tree_add<(SUML >= 3)>(r[0][q], r[1][q]);
-    }
+    for (int q = 0; q < 4; ++q) v[q] = tree_add<(SUML >= 3)>(p[0][q], p[1][q]);
     // bits 9..7: threads t and t + 128, t + 64, t + 32 through shared memory
 #pragma unroll
     for (int q = 0; q < 4; ++q) red[t][q] = v[q];
