@@ -74,6 +74,9 @@ __device__ __forceinline__ void mixed_pass(const SingleArgs &a, int64_t c0, int6
 template <int KX, int KY, int U, int CACHE, bool XY, int EMU>
 __global__ void __launch_bounds__(max_threads<4, U, 1, XY, EMU>())
     wxpy_mixed_kernel(const SingleArgs a) {
+    // the chunks of this thread's first pass, prefetched into L2 before the
+    // wait as in the family's kernel (single_kernel.cuh)
+    prefetch_first_pass<4, U, XY>(a, (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x, blockDim.x);
     pdl_enter();
     const int64_t tpb = blockDim.x;
     const int64_t stride = (int64_t)gridDim.x * tpb * U;
