@@ -745,23 +745,31 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
         rows.append(row)
     for k in (24, 26, 28):
         n = 1 << k
+        # the same timing rule as the step's calls: a short call is timed as a
+        # batch of calls on disjoint slices, 256-byte steps apart
+        nb = flushed_batch(n)
+        stride = 8 * ((n + 64 + 31) // 32 * 32)  # bytes
         for (name, ox, oy, ow, al) in CLASS_CASES:
-            a, b, c = px + ox, py + oy, pw + ow
-            if al == "w=x":
-                c = a
-            elif al == "w=y":
-                c = b
-            elif al == "x=y":
-                b = a
+            assert max(ox, oy, ow) // 8 + (nb - 1) * stride // 8 + n <= x.numel()
+            batch = []
+            for i in range(nb):
+                a, b, c = px + ox + i * stride, py + oy + i * stride, pw + ow + i * stride
+                if al == "w=x":
+                    c = a
+                elif al == "w=y":
+                    c = b
+                elif al == "x=y":
+                    b = a
+                batch.append((n, call_alpha(alpha, al), a, b, c, sh))
             nbytes = (16 if al == "x=y" else 24) * n
-            v, src = lookup_ptr(wx, n, a, b, c)
-            ms = time_flushed(lib, torch, stream, flush, [(n, call_alpha(alpha, al), a, b, c, sh)],
-                              reps)
+            v, src = lookup_ptr(wx, n, *batch[0][2:5])
+            ms = time_flushed(lib, torch, stream, flush, batch, reps)
             gbs = nbytes / (ms / 1e3) / 1e9
             rows.append({"n": n, "case": name, "alias": al, "x_offset_bytes": ox,
                          "y_offset_bytes": oy, "w_offset_bytes": ow,
                          "bytes_per_elem": nbytes // n, "variant": v["id"],
                          "vec_bytes": v["vec_bytes"], "variant_source": src,
+                         "calls_per_flushed_run": nb,
                          "gbs_l2_flushed": gbs, "us_l2_flushed": ms * 1e3,
                          "frac_of_peak_flushed": gbs / peak})
     del flush
