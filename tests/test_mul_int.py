@@ -112,6 +112,58 @@ def test_exact_ties_round_to_even(lib):
         assert check(lib, a, np.full(m, short)) == (0, m)
 
 
+def _sqrt_mod_pow2(r, k):
+    """An odd x with x*x = r (mod 2^k), for r = 1 (mod 8) (Hensel lifting)."""
+    x = 1
+    for i in range(3, k):
+        if ((x * x - r) >> i) & 1:
+            x += 1 << (i - 1)
+    assert (x * x - r) % (1 << k) == 0
+    return x
+
+
+def test_just_above_a_tie_by_the_lowest_word(lib):
+    """Products whose discarded part is one half plus a few units in the lowest
+    32 bits of the 106-bit product (bits 32 up to the round bit all zero): only
+    those low bits say the product is above the tie, so they must count as
+    sticky -- with the kept part even, dropping them would round down.  Made
+    from exact integers: B = A^-1 R modulo 2^(52 + t) for a chosen remainder
+    R = 2^(51 + t) + d, 0 < d < 2^32; squares from a square root of R modulo
+    2^(52 + t)."""
+    rng = np.random.default_rng(25)
+    big = 1 << 52
+    pa, pb, sq = [], [], []
+    while len(pa) < 4000 or len(sq) < 2000:
+        t = int(rng.integers(0, 2))
+        mod = 1 << (52 + t)
+        d = int(rng.integers(1, 1 << 32))
+        r = (1 << (51 + t)) + d
+        if len(pa) < 4000:
+            A = big + 2 * int(rng.integers(0, big // 2)) + 1  # odd: invertible modulo 2^k
+            B = (pow(A, -1, mod) * r) % mod
+            if big <= B < 2 * big and (A * B >= 1 << 105) == bool(t):
+                P = A * B
+                assert P % mod == r and (P >> (52 + t)) % 2 in (0, 1)
+                pa.append(A)
+                pb.append(B)
+        if len(sq) < 2000 and d % 8 == 1:
+            x = _sqrt_mod_pow2(r, 52 + t)
+            for A in (x % big + big, (mod - x) % big + big):
+                if (A * A >= 1 << 105) == bool(t) and (A * A) % mod == r:
+                    sq.append(A)
+    kept_even = sum(((A * B) >> 52 >> ((A * B) >> 105)) % 2 == 0 for A, B in zip(pa, pb))
+    assert kept_even > 1000  # the case where a lost sticky bit would round the wrong way
+    e = rng.integers(-400, 400, len(pa))
+    a = np.ldexp(np.array(pa, dtype=np.float64) * 2.0 ** -52, e)
+    b = np.ldexp(np.array(pb, dtype=np.float64) * 2.0 ** -52, -e // 2)
+    assert all(int(v) == A for v, A in zip(np.array(pa, dtype=np.float64), pa))  # exact
+    for s in (1.0, -1.0):
+        assert check(lib, s * a, b) == (0, len(a))
+    q = np.array(sq, dtype=np.float64) * 2.0 ** -52
+    assert check(lib, q) == (0, len(q))
+    assert check(lib, -np.ldexp(q, 100)) == (0, len(q))
+
+
 def test_normal_range_edges_and_slow_flags(lib):
     """Products whose unrounded exponent lands at and around both ends of the
     normal range: the fast path covers exactly the documented domain, and is
