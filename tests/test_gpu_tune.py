@@ -144,14 +144,26 @@ print("traced ok")
 
 def test_launch_bound_cells_get_a_fixed_choice():
     """n = 1024: every shape, the plain reference variant included, times at the
-    launch floor, so the search marks the cell launch-bound and stores the
-    first candidate within the tie band.  n = 2^26: the vector shapes beat the
+    launch floor (about 1.3 us a call), so the search marks the cell
+    launch-bound and stores the first candidate within the tie band.  Timings
+    this short carry noise of the band's own size, so each search is checked
+    against the rule whichever way it went (marked: the reference within the
+    band and several ties; not marked: the reference outside it), and at least
+    one of three must mark the cell.  n = 2^26: the vector shapes beat the
     plain variant by far more than the band, so the cell is not launch-bound."""
-    r = wx.wxpy_tune(1024, wx.TUNE_QUICK)
-    assert r["launch_bound"] == 1 and r["ties"] >= 2, r
-    assert r["reference_us"] <= r["best_us"] * 1.03 + 0.05
-    key = r["tune_key"]
-    assert wx.wxpy_tune_get(key) == r["best"]["id"]
+    marked = 0
+    for _ in range(3):
+        r = wx.wxpy_tune(1024, wx.TUNE_QUICK)
+        if r["launch_bound"]:
+            assert r["ties"] >= 2, r
+            assert r["reference_us"] <= r["best_us"] * 1.03 + 1e-6, r
+            marked += 1
+        else:
+            assert r["reference_us"] > r["best_us"] * 1.03, r
+        assert wx.wxpy_tune_get(r["tune_key"]) == r["best"]["id"]
+        if marked:
+            break
+    assert marked, r
     big = wx.wxpy_tune(1 << 26, wx.TUNE_QUICK)
     assert big["launch_bound"] == 0, big
     assert big["reference_us"] > big["best_us"] * 1.03
