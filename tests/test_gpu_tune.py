@@ -33,7 +33,10 @@ def test_full_search_selects_and_is_used(n):
     r = wx.wxpy_tune(n)
     assert r["rejected"] == 0 and r["candidates"] >= 20
     assert r["bucket"] == n.bit_length() - 1
-    assert r["best_us"] > 0 and r["best_us"] <= r["default_us"] * 1.0001
+    # the faster of the winner and the default; in a launch-bound cell the first
+    # candidate within the 3 % tie band of the faster one
+    band = 1.03 if r["launch_bound"] else 1.0001
+    assert r["best_us"] > 0 and r["best_us"] <= r["default_us"] * band + 1e-6, r
     assert wx.wxpy_tune_get(r["tune_key"]) == r["best"]["id"]
     alpha, xh, yh, gx, gy, gw = _case(n)
     v, src = wx.wxpy_lookup(gx.t, gy.t, gw.t)
