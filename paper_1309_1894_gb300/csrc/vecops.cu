@@ -93,6 +93,17 @@ __device__ __forceinline__ void products(const Coefs &c, const double (&e)[NIN],
     }
 }
 
+// The fast path of the integer-pipeline products alone: p[j] as in
+// products<1>, with `slow` set when any of them left the fast path (its
+// bits are then meaningless and the caller recomputes the element).
+template <int K, int NIN>
+__device__ __forceinline__ void products_fast(const Coefs &c, const double (&e)[NIN], double (&p)[K],
+                                              bool &slow) {
+    constexpr int F = NIN - K;
+#pragma unroll
+    for (int j = 0; j < K; ++j) p[j] = double_of(mul_rn_core(c.m[j], bits_of(e[F + j]), slow));
+}
+
 template <int OFF>
 struct AxpbyOp {
     static constexpr int kIn = 2;  // x, y
@@ -101,6 +112,12 @@ struct AxpbyOp {
     __device__ __forceinline__ static double apply(const Coefs &c, const double (&e)[kIn]) {
         double p[2];
         products<PM>(c, e, p);
+        return add_sel<OFF>(p[0], p[1], 1);
+    }
+    __device__ __forceinline__ static double apply_fast(const Coefs &c, const double (&e)[kIn],
+                                                        bool &slow) {
+        double p[2];
+        products_fast(c, e, p, slow);
         return add_sel<OFF>(p[0], p[1], 1);
     }
 };
@@ -116,6 +133,13 @@ struct AxpbypczOp {
         const double s1 = add_sel<OFF>(p[0], p[1], 1);
         return add_sel<OFF>(s1, p[2], OFF == 1 ? 0 : 1);
     }
+    __device__ __forceinline__ static double apply_fast(const Coefs &c, const double (&e)[kIn],
+                                                        bool &slow) {
+        double p[3];
+        products_fast(c, e, p, slow);
+        const double s1 = add_sel<OFF>(p[0], p[1], 1);
+        return add_sel<OFF>(s1, p[2], OFF == 1 ? 0 : 1);
+    }
 };
 
 template <int M, int OFF>
@@ -126,6 +150,15 @@ struct MaxpyOp {
     __device__ __forceinline__ static double apply(const Coefs &c, const double (&e)[kIn]) {
         double p[M];
         products<PM>(c, e, p);
+        double acc = e[0];
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc = add_sel<OFF>(acc, p[j], j + 1);
+        return acc;
+    }
+    __device__ __forceinline__ static double apply_fast(const Coefs &c, const double (&e)[kIn],
+                                                        bool &slow) {
+        double p[M];
+        products_fast(c, e, p, slow);
         double acc = e[0];
 #pragma unroll
         for (int j = 0; j < M; ++j) acc = add_sel<OFF>(acc, p[j], j + 1);
@@ -295,10 +328,44 @@ __device__ __forceinline__ void st_global_v2_cs(double *p, double a, double b) {
     asm volatile("st.global.cs.v2.f64 [%0], {%1,%2};" ::"l"(p), "d"(a), "d"(b) : "memory");
 }
 
+// This thread's elements of a tile, every product in FP64 (PM 0), from the
+// stage, which is still held.  Out of line: it runs only when an integer-
+// pipeline product left its fast path, and inlined it would be issued,
+// predicated off, on the FP64 pipeline for every tile.
+template <class Op, int TE>
+__device__ __noinline__ void staged_tile_fp64(const Coefs *cf, const double *sb, double *out,
+                                              int len, int c) {
+    constexpr int NIN = Op::kIn;
+    for (int j = 0; j < TE / 512; ++j) {
+        const int p = 2 * c + 512 * j;
+        if (p < len) {
+            double v[NIN][2];
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) ld_shared_v2(sb + k * TE + p, v[k][0], v[k][1]);
+            double r[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                double e[NIN];
+#pragma unroll
+                for (int k = 0; k < NIN; ++k) e[k] = v[k][q];
+                r[q] = Op::template apply<0>(*cf, e);
+            }
+            st_global_v2_cs(out + p, r[0], r[1]);
+        }
+    }
+}
+
+// PM = 1: the integer-pipeline products take their fast path with no test
+// between them and the sums, so the tile's arithmetic is one straight run
+// that the compiler can interleave (one element's FP64 sums with another's
+// integer products); if any product left the fast path, the thread's
+// elements are recomputed in FP64 and written again (nothing reads them
+// before the kernel ends, and the stage still holds the inputs).
 template <class Op, int PM, int TE>
 __device__ __forceinline__ void staged_tile(const Coefs &cf, const double *sb, double *out, int len,
                                             int c) {
     constexpr int NIN = Op::kIn;
+    bool slow = false;
 #pragma unroll
     for (int j = 0; j < TE / 512; ++j) {
         const int p = 2 * c + 512 * j;
@@ -312,16 +379,20 @@ __device__ __forceinline__ void staged_tile(const Coefs &cf, const double *sb, d
                 double e[NIN];
 #pragma unroll
                 for (int k = 0; k < NIN; ++k) e[k] = v[k][q];
-                r[q] = Op::template apply<PM>(cf, e);
+                if constexpr (PM == 1) r[q] = Op::apply_fast(cf, e, slow);
+                else r[q] = Op::template apply<0>(cf, e);
             }
             st_global_v2_cs(out + p, r[0], r[1]);
         }
+    }
+    if constexpr (PM == 1) {
+        if (slow) staged_tile_fp64<Op, TE>(&cf, sb, out, len, c);
     }
 }
 
 template <class Op>
 __global__ void __launch_bounds__(kStagedThreads, StageShape<Op::kIn>::kMinBlocks)
-    ew_staged_kernel(const EwArgs<Op::kIn> a) {
+    ew_staged_kernel(const __grid_constant__ EwArgs<Op::kIn> a) {
     constexpr int NIN = Op::kIn;
     using SS = StageShape<NIN>;
     constexpr int TE = SS::kTile, S = SS::kStages;
