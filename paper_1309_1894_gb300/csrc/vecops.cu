@@ -329,13 +329,17 @@ __device__ __forceinline__ void st_global_v2_cs(double *p, double a, double b) {
 }
 
 // This thread's elements of a tile, every product in FP64 (PM 0), from the
-// stage, which is still held.  Out of line: it runs only when an integer-
-// pipeline product left its fast path, and inlined it would be issued,
-// predicated off, on the FP64 pipeline for every tile.
+// stage, which is still held; d: the launch's coefficients.  Out of line: it
+// runs only when an integer-pipeline product left its fast path, and inlined
+// it would be issued, predicated off, on the FP64 pipeline for every tile.
 template <class Op, int TE>
-__device__ __noinline__ void staged_tile_fp64(const Coefs *cf, const double *sb, double *out,
-                                              int len, int c) {
+__device__ __noinline__ void staged_tile_fp64(double d0, double d1, double d2, double d3,
+                                              double d4, double d5, double d6, double d7,
+                                              const double *sb, double *out, int len, int c) {
     constexpr int NIN = Op::kIn;
+    Coefs cf;  // the FP64 products read only the doubles
+    cf.d[0] = d0, cf.d[1] = d1, cf.d[2] = d2, cf.d[3] = d3;
+    cf.d[4] = d4, cf.d[5] = d5, cf.d[6] = d6, cf.d[7] = d7;
     for (int j = 0; j < TE / 512; ++j) {
         const int p = 2 * c + 512 * j;
         if (p < len) {
@@ -348,7 +352,7 @@ __device__ __noinline__ void staged_tile_fp64(const Coefs *cf, const double *sb,
                 double e[NIN];
 #pragma unroll
                 for (int k = 0; k < NIN; ++k) e[k] = v[k][q];
-                r[q] = Op::template apply<0>(*cf, e);
+                r[q] = Op::template apply<0>(cf, e);
             }
             st_global_v2_cs(out + p, r[0], r[1]);
         }
@@ -386,13 +390,15 @@ __device__ __forceinline__ void staged_tile(const Coefs &cf, const double *sb, d
         }
     }
     if constexpr (PM == 1) {
-        if (slow) staged_tile_fp64<Op, TE>(&cf, sb, out, len, c);
+        if (slow)
+            staged_tile_fp64<Op, TE>(cf.d[0], cf.d[1], cf.d[2], cf.d[3], cf.d[4], cf.d[5], cf.d[6],
+                                     cf.d[7], sb, out, len, c);
     }
 }
 
 template <class Op>
 __global__ void __launch_bounds__(kStagedThreads, StageShape<Op::kIn>::kMinBlocks)
-    ew_staged_kernel(const __grid_constant__ EwArgs<Op::kIn> a) {
+    ew_staged_kernel(const EwArgs<Op::kIn> a) {
     constexpr int NIN = Op::kIn;
     using SS = StageShape<NIN>;
     constexpr int TE = SS::kTile, S = SS::kStages;
