@@ -718,6 +718,28 @@ CLASS_CASES = (("distinct", 0, 0, 0, "distinct"), ("w=x", 0, 0, 0, "w=x"),
                ("mixed 16/0/8", 16, 0, 8, "distinct"))
 
 
+def class_batch(px, py, pw, numel, n, ox, oy, ow, alias):
+    """(x, y, w) addresses of the calls that time one class row: the step's
+    own rule (flushed_batch), so a short call is a batch of calls on disjoint
+    slices of the three buffers (numel doubles each, at px, py, pw), 256-byte
+    steps apart so every slice keeps the row's offsets; the alias relation
+    holds within every call."""
+    nb = flushed_batch(n)
+    stride = 8 * ((n + 64 + 31) // 32 * 32)  # bytes
+    assert max(ox, oy, ow) // 8 + (nb - 1) * stride // 8 + n <= numel
+    out = []
+    for i in range(nb):
+        a, b, c = px + ox + i * stride, py + oy + i * stride, pw + ow + i * stride
+        if alias == "w=x":
+            c = a
+        elif alias == "w=y":
+            c = b
+        elif alias == "x=y":
+            b = a
+        out.append((a, b, c))
+    return out
+
+
 def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=9):
     """GB/s per call of the step, median of ``reps`` with the L2 flushed (read
     of a 512 MB buffer) before each timed run -- one call, or a batch of calls
@@ -745,22 +767,9 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
         rows.append(row)
     for k in (24, 26, 28):
         n = 1 << k
-        # the same timing rule as the step's calls: a short call is timed as a
-        # batch of calls on disjoint slices, 256-byte steps apart
-        nb = flushed_batch(n)
-        stride = 8 * ((n + 64 + 31) // 32 * 32)  # bytes
         for (name, ox, oy, ow, al) in CLASS_CASES:
-            assert max(ox, oy, ow) // 8 + (nb - 1) * stride // 8 + n <= x.numel()
-            batch = []
-            for i in range(nb):
-                a, b, c = px + ox + i * stride, py + oy + i * stride, pw + ow + i * stride
-                if al == "w=x":
-                    c = a
-                elif al == "w=y":
-                    c = b
-                elif al == "x=y":
-                    b = a
-                batch.append((n, call_alpha(alpha, al), a, b, c, sh))
+            batch = [(n, call_alpha(alpha, al), a, b, c, sh)
+                     for (a, b, c) in class_batch(px, py, pw, x.numel(), n, ox, oy, ow, al)]
             nbytes = (16 if al == "x=y" else 24) * n
             v, src = lookup_ptr(wx, n, *batch[0][2:5])
             ms = time_flushed(lib, torch, stream, flush, batch, reps)
@@ -769,7 +778,7 @@ def measure_sweep(wx, lib, torch, x, y, w, alpha, calls, sh, stream, peak, reps=
                          "y_offset_bytes": oy, "w_offset_bytes": ow,
                          "bytes_per_elem": nbytes // n, "variant": v["id"],
                          "vec_bytes": v["vec_bytes"], "variant_source": src,
-                         "calls_per_flushed_run": nb,
+                         "calls_per_flushed_run": len(batch),
                          "gbs_l2_flushed": gbs, "us_l2_flushed": ms * 1e3,
                          "frac_of_peak_flushed": gbs / peak})
     del flush
